@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark: segment-pair evaluations per second of the batched linking-number
+verify on one (or N) GB300, mixed precision against the all-FP64 direct sum.
+
+Workload (one "step"): verify every AABB-candidate loop pair of a seeded
+synthetic 4-in-1 chainmail sheet (2,048 rings of radius 1 x 256 segments on a
+32 x 64 grid, FP32 vertices; 11,653 candidate pairs, 7.6e8 segment pairs) --
+the whole hot path: pair frames, persistent tile sweep, careful re-sweep,
+FP64 recompute of near segment pairs, per-pair reduction and rounding.  The
+step is one replay of the CUDA graph that lk_plan_create captured; inputs are
+resident in HBM; L2 is flushed (256 MB write) before every timed step.
+
+`--impl reference` times the FP64 CPU oracle on the same workload instead.
+Under torchrun each rank verifies its own sheet (weak scaling, no collective
+on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "segment-pair evals/s and p99 verify latency, mixed-prec vs FP64, 1 GB300"
+UNIT = "segment-pair evals/s"
+# Algorithmic FP32 work per segment pair (FMA = 2 flops): the amortised
+# closed-form term with shared grid norms and edge dot products.
+FLOPS_PER_SP = 58.0
+# FP32 peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+KERNELS_PER_STEP = 5  # pair_frames, sweep_mixed, sweep_careful, near_fix, reduce
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(rank: int):
+    from paper_2106_12655_gb300 import workloads as W
+
+    g = W.chainmail(seed=2 + rank)
+    desc = ("4-in-1 chainmail sheet: 32x64 rings of radius 1, 256 segments each, FP32 vertices, "
+            "seeded perturbation sigma=0.02, all AABB-candidate pairs")
+    return g, desc
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(g):
+    from oracle import oracle as O
+
+    threads = O.default_threads()
+    t0 = time.perf_counter()
+    raw = O.link_pairs(g.vertices, g.offsets, g.pairs, threads=threads)
+    dt = time.perf_counter() - t0
+    return raw, {"value": g.segment_pairs() / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                 "sample": "all %d candidate pairs of the sheet, one pass (%.1f s)" % (g.pairs.shape[0], dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    g, desc = workload(0)
+    threads = O.default_threads()
+    rng = np.random.default_rng(0)
+    per_step = max(1, g.pairs.shape[0] // 16)
+    times, sps = [], []
+    for s in range(args.warmup + args.steps):
+        pick = rng.choice(g.pairs.shape[0], per_step, replace=False)
+        sub = g.pairs[pick]
+        t0 = time.perf_counter()
+        O.link_pairs(g.vertices, g.offsets, sub, threads=threads)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            sps.append(g.segment_pairs(sub))
+    value = sum(sps) / sum(times)
+    sample = "%d seeded random candidate pairs per step (1/16 of the sheet)" % per_step
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "pairs_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2106_12655_gb300 import build as B
+    from paper_2106_12655_gb300 import lk
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    lk.load()
+    g, desc = workload(rank)
+    n = g.pairs.shape[0]
+    sps_per_step = g.segment_pairs()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    v = torch.from_numpy(g.vertices).to(dev)
+    off = torch.from_numpy(g.offsets).to(dev)
+    pairs_d = torch.from_numpy(g.pairs).to(dev)
+    lk_o = torch.zeros(n, dtype=torch.int32, device=dev)
+    raw_o = torch.zeros(n, dtype=torch.float64, device=dev)
+    st_o = torch.zeros(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    opt = lk.lk_default_options()
+    opt.timing = 1
+    ctx = lk.lk_create(v, off, opt, stream)
+    plan = lk.lk_plan_create(ctx, pairs_d, stream)
+
+    def step_timed():
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lk.lk_plan_run(plan, lk_o, raw_o, st_o, stream, ctx=ctx)
+        e1.record(stream)
+        return e0, e1
+
+    for _ in range(args.warmup):
+        step_timed()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    step_ms, sweep_ms = [], []
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        e0, e1 = step_timed()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        sweep_ms.append(lk.lk_get_stats(ctx)["sweep_ms"])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    stats = lk.lk_get_stats(ctx)
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * sps_per_step * args.steps / (total_ms / 1e3)
+    lk_host = lk_o.cpu().numpy()
+    raw_host = raw_o.cpu().numpy()
+    st_host = st_o.cpu().numpy()
+
+    # All-FP64 direct sum on the same GPU and workload (the baseline to beat).
+    opt64 = lk.lk_default_options()
+    opt64.precision = lk.LK_ALL_F64
+    opt64.timing = 1
+    ctx64 = lk.lk_create(v, off, opt64, stream)
+    plan64 = lk.lk_plan_create(ctx64, pairs_d, stream)
+    lk64 = torch.zeros_like(lk_o)
+    raw64 = torch.zeros_like(raw_o)
+    st64 = torch.zeros_like(st_o)
+    lk.lk_plan_run(plan64, lk64, raw64, st64, stream, ctx=ctx64)
+    f64_ms = []
+    for _ in range(args.fp64_steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lk.lk_plan_run(plan64, lk64, raw64, st64, stream, ctx=ctx64)
+        e1.record(stream)
+        e1.synchronize()
+        f64_ms.append(e0.elapsed_time(e1))
+    fp64_value = sps_per_step / (statistics.median(f64_ms) / 1e3)
+    raw64_host = raw64.cpu().numpy()
+    lk.lk_plan_destroy(plan64)
+    lk.lk_destroy(ctx64)
+
+    # End to end through the public C-ABI call with host buffers: each step
+    # uploads a displacement of every vertex and the pair list from pinned
+    # host memory, verifies, and reads the results back to host memory.
+    rng = np.random.default_rng(11)
+    delta = torch.from_numpy(rng.normal(scale=1e-6, size=g.vertices.shape).astype(np.float32)).pin_memory()
+    neg = (-delta).pin_memory()
+    pairs_h = torch.from_numpy(g.pairs).pin_memory()
+    lk_h = torch.zeros(n, dtype=torch.int32).pin_memory()
+    raw_h = torch.zeros(n, dtype=torch.float64).pin_memory()
+    st_h = torch.zeros(n, dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for s in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lk.lk_update(ctx, delta if s % 2 == 0 else neg, True, stream)
+        lk.lk_verify(ctx, pairs_h, lk_h, raw_h, st_h, stream)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            e2e_ms.append(dt * 1e3)
+    e2e_value = world * sps_per_step * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+    h2d = delta.numel() * delta.element_size() + pairs_h.numel() * pairs_h.element_size()
+    d2h = n * (4 + 8 + 4)
+    e2e_ok = bool(np.all(st_h.numpy() == 0) and np.array_equal(lk_h.numpy(), lk_host))
+    lk.lk_plan_destroy(plan)
+    lk.lk_destroy(ctx)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    sweep_avg = statistics.mean(sweep_ms)
+    achieved = sps_per_step * FLOPS_PER_SP / (sweep_avg / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "precision": "FP32 segment-pair terms, FP64 accumulation, FP64 recompute of near pairs",
+        "data": "synthetic",
+        "config": {"workload": desc, "pairs": int(n), "segment_pairs_per_step": int(sps_per_step),
+                   "l2": "flushed before every timed step (256 MB write)", "step": "one CUDA-graph replay"},
+        "p50_verify_ms": float(np.percentile(step_ms, 50)), "p99_verify_ms": float(np.percentile(step_ms, 99)),
+        "fp64_baseline": {"value": fp64_value, "unit": UNIT, "ms_per_step": statistics.median(f64_ms),
+                          "speedup_mixed_over_fp64": value / world / fp64_value,
+                          "max_abs_raw_diff_vs_mixed": float(np.max(np.abs(raw64_host - raw_host)))},
+        "fp64_recomputed_segment_pairs": stats["fp64_pairs"], "careful_items": stats["careful_items"],
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "sweep_mixed_kernel",
+                     "kernel_ms": sweep_avg, "flops_per_segment_pair": FLOPS_PER_SP,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": statistics.mean(e2e_ms), "results_match_device_run": e2e_ok},
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "clocks": clk, "wall_s_timed_region": wall,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        ref_raw, cb = cpu_baseline(g)
+        line["cpu_baseline"] = cb
+        ref_lk = np.sign(ref_raw) * np.floor(np.abs(ref_raw) + 0.5)
+        line["parity_vs_oracle"] = {"lk_bit_exact": bool(np.array_equal(lk_host, ref_lk.astype(np.int32))),
+                                    "max_abs_raw_err": float(np.max(np.abs(raw_host - ref_raw))),
+                                    "all_status_ok": bool(np.all(st_host == 0))}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * lk.h -- C ABI of the GB300 linking-number library.
+ *
+ * The library computes Gauss linking numbers of closed polylines by direct
+ * summation of the closed-form segment-pair term over every segment pair of
+ * each requested loop pair, then rounds each per-pair sum to an integer
+ * (Qu & James, "Fast Linking Numbers for Topology Verification of Loopy
+ * Structures", SIGGRAPH 2021: Sec. 2.1 Eq. 3 and Eq. 4; Sec. 3.4.2,
+ * Algorithm 5; the certificate matrix of Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Geometry is CSR: vertices[n_vertices][3] (x,y,z interleaved, float32 or
+ *    float64) and loop_offsets[n_loops+1] (int64, offsets[0] = 0,
+ *    offsets[n_loops] = n_vertices, strictly increasing by >= 3).  Loop l owns
+ *    vertices offsets[l] .. offsets[l+1]-1 and closes implicitly: its last
+ *    vertex joins its first (Algorithm 5 indexes l_{j+1} with wrap-around).
+ *    Orientation is the vertex order.
+ *  - A loop pair is two int32 loop indices (a, b), a != b.  Loop a plays
+ *    gamma_1 (vertices l_j) and loop b gamma_2 (vertices k_i) of Eq. 4; the
+ *    linking number is symmetric in a and b.
+ *  - Pointers may be host memory or device memory of the current device; the
+ *    library tells them apart by CUDA unified addressing.  The caller owns
+ *    every buffer it passes; the library copies what it keeps.
+ *  - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).  Work
+ *    is ordered on that stream.
+ *  - Whole-call failures return a non-zero lk_status and set a message that
+ *    lk_last_error() returns; per-pair outcomes go to status_out[].
+ *  - Nothing in this library spins on device memory; no kernel waits for
+ *    another, so no call can hang on a missing peer.
+ */
+#ifndef LK_H_
+#define LK_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LK_OK = 0,
+    LK_ERR_ARG = 1,          /* invalid argument (whole call) or invalid pair (per pair) */
+    LK_ERR_ZERO_SEGMENT = 2, /* a segment shorter than eps*xi (Sec. 3.3, Algorithm 3 input check) */
+    LK_ERR_INTERSECT = 3,    /* the loops meet: Eq. 4 is singular there (Sec. 4.1, robustness) */
+    LK_ERR_NONINTEGER = 4,   /* |raw - round(raw)| > int_tol: result not trustworthy */
+    LK_ERR_OOM = 5,          /* device allocation failed or the memory budget is exceeded */
+    LK_ERR_TIMEOUT = 6,      /* reserved: no call waits on the device, so none returns it */
+    LK_ERR_CUDA = 7,         /* a CUDA runtime error (message in lk_last_error) */
+    LK_ERR_BUSY = 8          /* the server has no free slot / memory for this request now */
+} lk_status;
+
+typedef enum { LK_F32 = 0, LK_F64 = 1 } lk_dtype;
+
+typedef enum {
+    /* FP32 bulk sweep with FP64 accumulation; segment pairs closer than
+     * near_ratio segment lengths are recomputed in FP64. */
+    LK_MIXED = 0,
+    /* every segment pair in FP64 with two atan2 per pair (Algorithm 5 as
+     * written): the plain all-FP64 GPU direct sum. */
+    LK_ALL_F64 = 1
+} lk_precision;
+
+typedef struct lk_options {
+    int precision;       /* lk_precision, default LK_MIXED */
+    double near_ratio;   /* tau >= 4: a segment pair (j,i) with |l_j - k_i| < tau*max(|s_j|,|s_i|)
+                            is evaluated in FP64 (default 4.0) */
+    double int_tol;      /* per-pair status LK_ERR_NONINTEGER when |raw - lk| > int_tol (default 0.1) */
+    size_t mem_budget;   /* device bytes one verify may use for its work buffers, 0 = unlimited */
+    int tile_rows;       /* rows per work item; 0 = chosen by the built-in tuner */
+    int near_capacity;   /* entries of the FP64 recompute list (default 1<<20); overflow is
+                            evaluated in place, results are unchanged */
+    int timing;          /* 1: time the bulk sweep kernel with CUDA events on the launch stream
+                            (read back by lk_get_stats as sweep_ms); default 0 */
+    int64_t accurate_threshold; /* LK_MIXED: loop pairs with at least this many segment pairs use
+                            the bias-free FP32 arithmetic (refined sqrt and division, shifted
+                            denominators); smaller pairs use the hardware approximations,
+                            whose relative bias (~5e-9) is negligible for them.  0 = always
+                            accurate; default 1<<22 */
+} lk_options;
+
+typedef struct lk_stats {
+    int64_t n_pairs;          /* pairs in the last verify */
+    int64_t n_items;          /* work items (tiles) of the last verify */
+    int64_t segment_pairs;    /* segment pairs evaluated by the last verify */
+    int64_t fp64_pairs;       /* of those, recomputed in FP64 (LK_MIXED) */
+    int64_t near_overflow;    /* FP64 recomputes that did not fit the list */
+    int32_t tile_rows;        /* rows per work item used */
+    int32_t tile_cols;        /* columns per work item used */
+    int64_t careful_items;    /* items swept again with per-pair tests */
+    double sweep_ms;          /* bulk sweep kernel time (options.timing = 1), else -1 */
+} lk_stats;
+
+typedef struct lk_ctx lk_ctx;
+typedef struct lk_plan lk_plan;
+typedef struct lk_server lk_server;
+
+/* Fill *opt with the defaults listed above. */
+void lk_default_options(lk_options* opt);
+
+/*
+ * Create a context holding one CSR geometry resident in device memory (the
+ * loops Gamma_i of Algorithm 1, already discretised into polylines).
+ *  out          : receives the context (caller destroys it with lk_destroy).
+ *  vertices     : [n_vertices][3] of vdtype, host or device.
+ *  loop_offsets : [n_loops+1] int64, host or device.
+ *  opt          : NULL for defaults.
+ * Errors: LK_ERR_ARG (bad sizes, offsets, fewer than 3 vertices in a loop,
+ * non-finite coordinates), LK_ERR_ZERO_SEGMENT (a segment of length < eps*xi,
+ * xi the mean absolute coordinate and eps the machine epsilon of vdtype:
+ * Algorithm 3's input check), LK_ERR_OOM, LK_ERR_CUDA.  On error *out is NULL.
+ * The call returns after the geometry is on the device.
+ */
+lk_status lk_create(lk_ctx** out, const void* vertices, lk_dtype vdtype, int64_t n_vertices,
+                    const int64_t* loop_offsets, int64_t n_loops, const lk_options* opt,
+                    void* cuda_stream);
+
+/*
+ * Replace the resident vertices (is_delta = 0) or add a displacement to each
+ * (is_delta = 1), keeping the loop structure: one simulation step of the
+ * verification loop of Sec. 5 ("compare M_t with M_0").
+ *  data : [n_vertices][3] of dtype, host or device.
+ * Enqueued on cuda_stream; later work on that stream sees the new geometry.
+ * Errors: LK_ERR_ARG, LK_ERR_CUDA.  No zero-length check is made here; a
+ * degenerate step shows up as LK_ERR_INTERSECT in the verify that follows.
+ */
+lk_status lk_update(lk_ctx* ctx, const void* data, lk_dtype dtype, int is_delta, void* cuda_stream);
+
+/*
+ * Linking numbers of n_pairs loop pairs (the loop over P in Algorithm 1, every
+ * pair by the direct sum of Sec. 3.4.2) in one batched persistent launch.
+ *  loop_pairs : [n_pairs][2] int32, host or device.
+ *  lk_out     : [n_pairs] int32, the rounded linking numbers (may be NULL).
+ *  raw_out    : [n_pairs] double, the unrounded FP64 sums (may be NULL).
+ *  status_out : [n_pairs] int32 lk_status per pair (may be NULL): LK_OK,
+ *               LK_ERR_ARG (a == b or out of range), LK_ERR_INTERSECT,
+ *               LK_ERR_NONINTEGER.  A pair that is not LK_OK has lk_out = 0.
+ * Outputs may be host or device memory.  When any output is host memory the
+ * call returns with the results written; otherwise it returns after enqueueing
+ * and the results are valid once cuda_stream has reached the call's end
+ * (lk_sync).  n_pairs = 0 is allowed and does nothing.
+ * Errors: LK_ERR_ARG, LK_ERR_OOM (mem_budget exceeded or allocation failed),
+ * LK_ERR_CUDA.
+ */
+lk_status lk_verify(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, int32_t* lk_out,
+                    double* raw_out, int32_t* status_out, void* cuda_stream);
+
+/* Wait until all work the context enqueued on cuda_stream has finished. */
+lk_status lk_sync(lk_ctx* ctx, void* cuda_stream);
+
+/* Statistics of the most recent completed verify or plan run on this context. */
+lk_status lk_get_stats(lk_ctx* ctx, lk_stats* out);
+
+/* Free the context and its device memory.  NULL is ignored. */
+void lk_destroy(lk_ctx* ctx);
+
+/* The message of the last failed call on ctx (ctx may be NULL: the last
+ * failure of lk_create or of a call given a NULL context). */
+const char* lk_last_error(const lk_ctx* ctx);
+
+/*
+ * A plan fixes one pair list and captures the whole verify (pair set-up,
+ * persistent tile sweep, FP64 recompute, per-pair reduction) as a CUDA graph,
+ * so that a simulation loop re-verifies the same certificate after each
+ * lk_update with one graph launch (Sec. 5 verification loop; Algorithm 1).
+ *  loop_pairs : copied at creation; later changes to the caller's array are
+ *               not seen.
+ * lk_plan_run writes the same outputs as lk_verify (same rules for host and
+ * device memory).  Plans hold device memory until lk_plan_destroy, and must
+ * be destroyed before their context.
+ */
+lk_status lk_plan_create(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, lk_plan** out,
+                         void* cuda_stream);
+lk_status lk_plan_run(lk_plan* plan, int32_t* lk_out, double* raw_out, int32_t* status_out,
+                      void* cuda_stream);
+void lk_plan_destroy(lk_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LK_H_ */

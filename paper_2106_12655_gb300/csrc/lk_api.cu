@@ -1,0 +1,705 @@
+// Host runtime of the linking-number library: the C ABI of include/lk.h.
+//
+// A context keeps one CSR geometry resident on the device (FP64 vertices
+// padded to 32 bytes, loop offsets, loop boxes).  A verify packs the pair list
+// on the host into work items (tiles of one pair: 128 column segments by
+// tile_rows row segments, ordered by decreasing cost), uploads the item
+// tables, and enqueues on the caller's stream: pair frames -> persistent bulk
+// sweep -> careful sweep of handed-over items -> FP64 recompute of near
+// segment pairs -> fixed-order per-pair reduction (Algorithm 1's loop over P,
+// each ComputeLink being the direct sum of Sec. 3.4.2).  A plan captures the
+// same device sequence once in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "lk.h"
+#include "lk_internal.h"
+
+using lk::NearEntry;
+using lk::PairTask;
+using lk::Vtx;
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_last_error = "";
+
+void set_global_error(const std::string& m) {
+    std::lock_guard<std::mutex> g(g_err_mu);
+    g_last_error = m;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t cap = 0;  // elements
+    cudaError_t ensure(size_t n) {
+        if (n <= cap && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        const size_t want = std::max<size_t>(n, 1);
+        cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    size_t bytes_for(size_t n) const { return std::max<size_t>(n, 1) * sizeof(T); }
+};
+
+struct Packed {
+    std::vector<PairTask> tasks;
+    std::vector<int64_t> item_begin;
+    std::vector<int32_t> item_task;
+    int64_t n_items = 0;
+    int64_t n_acc_items = 0;   // items [0, n_acc_items) belong to accurate-variant pairs
+    int64_t segment_pairs = 0;
+    int tile_rows_max = 0;
+    int tile_cols = 0;
+};
+
+// Device working memory of one verify (grow-only, reused across calls).
+struct Workspace {
+    DevBuf<PairTask> tasks;
+    DevBuf<int64_t> item_begin;
+    DevBuf<int32_t> item_task;
+    DevBuf<double> partial;
+    DevBuf<int64_t> careful_items;
+    DevBuf<NearEntry> near_list;
+    DevBuf<unsigned long long> fix_acc;
+    DevBuf<unsigned long long> fp64_count;
+    DevBuf<int> flags;
+    DevBuf<unsigned long long> counters;  // [0] accurate-sweep counter, [1] overflow,
+                                          // [2] u32 careful_count, careful_counter,
+                                          // [3] u32 near_count, unused, [4] fast-sweep / f64 counter
+    DevBuf<int32_t> lk;
+    DevBuf<double> raw;
+    DevBuf<int32_t> status;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the bulk sweep (options.timing)
+
+    cudaError_t events() {
+        cudaError_t e = cudaSuccess;
+        if (!ev0) e = cudaEventCreate(&ev0);
+        if (e == cudaSuccess && !ev1) e = cudaEventCreate(&ev1);
+        return e;
+    }
+
+    void release() {
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        ev0 = ev1 = nullptr;
+        tasks.release(); item_begin.release(); item_task.release(); partial.release();
+        careful_items.release(); near_list.release(); fix_acc.release(); fp64_count.release();
+        flags.release(); counters.release(); lk.release(); raw.release(); status.release();
+    }
+};
+
+}  // namespace
+
+struct lk_ctx {
+    int device = 0;
+    int num_sms = 1;
+    lk_options opt;
+    int64_t n_vertices = 0;
+    int64_t n_loops = 0;
+    std::vector<int64_t> h_offsets;
+    Vtx* d_V = nullptr;
+    int64_t* d_offsets = nullptr;
+    double* d_aabb = nullptr;
+    void* d_stage = nullptr;  // staging for host-side lk_update data
+    size_t stage_bytes = 0;
+    Workspace ws;
+    lk_stats stats{};
+    int64_t stats_tasks = 0;        // tasks of the last verify (for lazy FP64 counts)
+    bool stats_pending = false;
+    const unsigned long long* stats_fp64 = nullptr;
+    const unsigned long long* stats_overflow = nullptr;
+    const unsigned int* stats_careful = nullptr;
+    cudaEvent_t stats_ev0 = nullptr, stats_ev1 = nullptr;
+    cudaStream_t stats_stream = nullptr;
+    std::string err;
+};
+
+struct lk_plan {
+    lk_ctx* ctx = nullptr;
+    Packed pk;
+    Workspace ws;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t capture = nullptr;
+};
+
+namespace {
+
+lk_status fail(lk_ctx* ctx, lk_status st, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    set_global_error(msg);
+    return st;
+}
+
+lk_status cuda_fail(lk_ctx* ctx, cudaError_t e, const char* where) {
+    const lk_status st = (e == cudaErrorMemoryAllocation) ? LK_ERR_OOM : LK_ERR_CUDA;
+    return fail(ctx, st, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LK_CUDA(ctx, call)                                  \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+int default_tile_rows(int64_t n_rows, int64_t n_cols, int tile_cols, int user_rows) {
+    if (user_rows > 0) return user_rows;
+    const int64_t col_tiles = (n_cols + tile_cols - 1) / tile_cols;
+    int64_t row_tiles = (n_rows + 255) / 256;
+    const int64_t max_items_per_pair = 1 << 16;
+    if (col_tiles * row_tiles > max_items_per_pair)
+        row_tiles = std::max<int64_t>(1, max_items_per_pair / col_tiles);
+    int64_t rows = (n_rows + row_tiles - 1) / row_tiles;
+    rows = (rows + lk::kChunkRows - 1) / lk::kChunkRows * lk::kChunkRows;
+    return (int)std::min<int64_t>(rows, INT32_MAX);
+}
+
+// Work items of a pair list.  Loop a of a pair plays gamma_1 of Eq. 4 and loop
+// b gamma_2; the term is symmetric under exchanging them (Eq. 1), so the
+// longer loop becomes the row loop (iterated) and the other the column loop
+// (spread over lanes).  The tiling of a pair depends on its two sizes only, so
+// a pair's result does not depend on the rest of the batch.
+lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
+    const bool f64 = ctx->opt.precision == LK_ALL_F64;
+    const int tile_cols = f64 ? lk::kF64TileCols : lk::kTileCols;
+    pk.tasks.assign((size_t)n, PairTask{});
+    pk.tile_cols = tile_cols;
+    pk.tile_rows_max = 0;
+    pk.segment_pairs = 0;
+    std::vector<int64_t> items((size_t)n, 0);
+    std::vector<double> cost((size_t)n, 0.0);
+    for (int64_t p = 0; p < n; ++p) {
+        PairTask& t = pk.tasks[(size_t)p];
+        t.out_index = (int32_t)p;
+        const int32_t a = pairs[2 * p], b = pairs[2 * p + 1];
+        if (a < 0 || b < 0 || a >= ctx->n_loops || b >= ctx->n_loops || a == b) {
+            t.status = LK_ERR_ARG;
+            continue;
+        }
+        const int64_t na = ctx->h_offsets[a + 1] - ctx->h_offsets[a];
+        const int64_t nb = ctx->h_offsets[b + 1] - ctx->h_offsets[b];
+        const bool a_rows = na >= nb;
+        t.row_loop = a_rows ? a : b;
+        t.col_loop = a_rows ? b : a;
+        t.row_base = ctx->h_offsets[t.row_loop];
+        t.col_base = ctx->h_offsets[t.col_loop];
+        t.n_rows = (int32_t)(a_rows ? na : nb);
+        t.n_cols = (int32_t)(a_rows ? nb : na);
+        t.tile_rows = default_tile_rows(t.n_rows, t.n_cols, tile_cols, ctx->opt.tile_rows);
+        t.col_tiles = (t.n_cols + tile_cols - 1) / tile_cols;
+        const int64_t row_tiles = (t.n_rows + t.tile_rows - 1) / t.tile_rows;
+        items[(size_t)p] = (int64_t)t.col_tiles * row_tiles;
+        cost[(size_t)p] = (double)std::min(t.tile_rows, t.n_rows) * std::min(tile_cols, t.n_cols);
+        t.status = LK_OK;
+        t.scale = 1.0;
+        t.accurate = (int64_t)t.n_rows * t.n_cols >= ctx->opt.accurate_threshold ? 1 : 0;
+        pk.segment_pairs += (int64_t)t.n_rows * t.n_cols;
+        pk.tile_rows_max = std::max(pk.tile_rows_max, t.tile_rows);
+    }
+    // Accurate-variant pairs first (they run in their own launch), then within
+    // each variant the largest items first, so that the persistent grid's
+    // tail is made of small ones.
+    std::vector<int64_t> order((size_t)n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+        const int ax = pk.tasks[(size_t)x].accurate, ay = pk.tasks[(size_t)y].accurate;
+        if (ax != ay) return ax > ay;
+        return cost[(size_t)x] > cost[(size_t)y];
+    });
+    std::vector<PairTask> sorted((size_t)n);
+    pk.item_begin.assign((size_t)n + 1, 0);
+    for (int64_t k = 0; k < n; ++k) {
+        sorted[(size_t)k] = pk.tasks[(size_t)order[(size_t)k]];
+        pk.item_begin[(size_t)k + 1] = pk.item_begin[(size_t)k] + items[(size_t)order[(size_t)k]];
+    }
+    pk.tasks.swap(sorted);
+    pk.n_items = pk.item_begin[(size_t)n];
+    pk.n_acc_items = 0;
+    for (int64_t k = 0; k < n; ++k)
+        if (pk.tasks[(size_t)k].accurate) pk.n_acc_items = pk.item_begin[(size_t)k + 1];
+    if (pk.n_items > (int64_t)INT32_MAX * 16)
+        return fail(ctx, LK_ERR_ARG, "lk_verify: too many work items");
+    pk.item_task.resize((size_t)pk.n_items);
+    for (int64_t k = 0; k < n; ++k)
+        std::fill(pk.item_task.begin() + pk.item_begin[(size_t)k],
+                  pk.item_task.begin() + pk.item_begin[(size_t)k + 1], (int32_t)k);
+    return LK_OK;
+}
+
+size_t workspace_bytes(const lk_ctx* ctx, int64_t n_tasks, int64_t n_items) {
+    const size_t near = (size_t)std::max(0, ctx->opt.near_capacity);
+    return n_tasks * (sizeof(PairTask) + 8 + 8 + 8 + 4 + 4 + 8 + 4) + n_items * (4 + 8 + 8) +
+           near * sizeof(NearEntry) + 64;
+}
+
+lk_status ensure_workspace(lk_ctx* ctx, Workspace& ws, int64_t n_tasks, int64_t n_items) {
+    if (ctx->opt.mem_budget > 0 && workspace_bytes(ctx, n_tasks, n_items) > ctx->opt.mem_budget)
+        return fail(ctx, LK_ERR_OOM, "lk_verify: work buffers exceed mem_budget");
+    const size_t nt = (size_t)std::max<int64_t>(n_tasks, 1), ni = (size_t)std::max<int64_t>(n_items, 1);
+    LK_CUDA(ctx, ws.tasks.ensure(nt));
+    LK_CUDA(ctx, ws.item_begin.ensure(nt + 1));
+    LK_CUDA(ctx, ws.item_task.ensure(ni));
+    LK_CUDA(ctx, ws.partial.ensure(ni));
+    LK_CUDA(ctx, ws.careful_items.ensure(ni));
+    LK_CUDA(ctx, ws.near_list.ensure((size_t)std::max(1, ctx->opt.near_capacity)));
+    LK_CUDA(ctx, ws.fix_acc.ensure(nt));
+    LK_CUDA(ctx, ws.fp64_count.ensure(nt));
+    LK_CUDA(ctx, ws.flags.ensure(nt));
+    LK_CUDA(ctx, ws.counters.ensure(8));
+    LK_CUDA(ctx, ws.lk.ensure(nt));
+    LK_CUDA(ctx, ws.raw.ensure(nt));
+    LK_CUDA(ctx, ws.status.ensure(nt));
+    if (ctx->opt.timing) LK_CUDA(ctx, ws.events());
+    return LK_OK;
+}
+
+lk_status upload_packed(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStream_t s) {
+    const int64_t n = (int64_t)pk.tasks.size();
+    if (n > 0)
+        LK_CUDA(ctx, cudaMemcpyAsync(ws.tasks.p, pk.tasks.data(), n * sizeof(PairTask),
+                                     cudaMemcpyHostToDevice, s));
+    LK_CUDA(ctx, cudaMemcpyAsync(ws.item_begin.p, pk.item_begin.data(), (n + 1) * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, s));
+    if (pk.n_items > 0)
+        LK_CUDA(ctx, cudaMemcpyAsync(ws.item_task.p, pk.item_task.data(),
+                                     pk.n_items * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    return LK_OK;
+}
+
+lk::SweepArgs sweep_args(const lk_ctx* ctx, Workspace& ws, const Packed& pk) {
+    lk::SweepArgs a{};
+    a.V = ctx->d_V;
+    a.tasks = ws.tasks.p;
+    a.item_begin = ws.item_begin.p;
+    a.item_task = ws.item_task.p;
+    a.n_items = pk.n_items;
+    a.partial = ws.partial.p;
+    a.item_counter = ws.counters.p + 4;
+    a.overflow = ws.counters.p + 1;
+    unsigned int* u32 = reinterpret_cast<unsigned int*>(ws.counters.p + 2);
+    a.careful_count = u32 + 0;
+    a.careful_counter = u32 + 1;
+    a.near_count = u32 + 2;   // low half of counters[3]
+    a.n_tasks = (int64_t)pk.tasks.size();
+    a.careful_items = ws.careful_items.p;
+    a.near_list = ws.near_list.p;
+    a.near_capacity = std::max(1, ctx->opt.near_capacity);
+    a.fix_acc = ws.fix_acc.p;
+    a.fp64_count = ws.fp64_count.p;
+    a.flags = ws.flags.p;
+    a.near_ratio_sq = (float)(ctx->opt.near_ratio * ctx->opt.near_ratio);
+    return a;
+}
+
+// Record a timing event; inside stream capture it must become an external
+// event-record node of the graph.
+cudaError_t record_event(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                                : cudaEventRecord(ev, s);
+}
+
+// The device sequence of one verify (graph-capturable: no host sync).
+lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStream_t s) {
+    const int64_t n = (int64_t)pk.tasks.size();
+    if (n == 0) return LK_OK;
+    LK_CUDA(ctx, cudaMemsetAsync(ws.counters.p, 0, 8 * sizeof(unsigned long long), s));
+    LK_CUDA(ctx, cudaMemsetAsync(ws.fix_acc.p, 0, n * sizeof(unsigned long long), s));
+    LK_CUDA(ctx, cudaMemsetAsync(ws.fp64_count.p, 0, n * sizeof(unsigned long long), s));
+    LK_CUDA(ctx, cudaMemsetAsync(ws.flags.p, 0, n * sizeof(int), s));
+    lk::launch_pair_frames(ws.tasks.p, n, ctx->d_aabb, s);
+    const lk::SweepArgs a = sweep_args(ctx, ws, pk);
+    if (pk.n_items > 0) {
+        if (ctx->opt.precision == LK_ALL_F64) {
+            const int grid = ctx->num_sms * lk::sweep_f64_blocks_per_sm();
+            if (ctx->opt.timing) LK_CUDA(ctx, record_event(ws.ev0, s));
+            lk::launch_sweep_f64(a, grid, s);
+            if (ctx->opt.timing) LK_CUDA(ctx, record_event(ws.ev1, s));
+        } else {
+            if (ctx->opt.timing) LK_CUDA(ctx, record_event(ws.ev0, s));
+            lk::launch_sweep_mixed(a, true, 0, pk.n_acc_items, ws.counters.p + 0,
+                                   ctx->num_sms * lk::sweep_mixed_blocks_per_sm(true), s);
+            lk::launch_sweep_mixed(a, false, pk.n_acc_items, pk.n_items, ws.counters.p + 4,
+                                   ctx->num_sms * lk::sweep_mixed_blocks_per_sm(false), s);
+            if (ctx->opt.timing) LK_CUDA(ctx, record_event(ws.ev1, s));
+            lk::launch_sweep_careful(a, ctx->num_sms, s);
+            lk::launch_near_fix(a, ctx->num_sms * 4, s);
+        }
+    }
+    lk::ReduceArgs r{};
+    r.tasks = ws.tasks.p;
+    r.item_begin = ws.item_begin.p;
+    r.partial = ws.partial.p;
+    r.fix_acc = ws.fix_acc.p;
+    r.flags = ws.flags.p;
+    r.n_tasks = n;
+    r.int_tol = ctx->opt.int_tol;
+    r.lk_out = ws.lk.p;
+    r.raw_out = ws.raw.p;
+    r.status_out = ws.status.p;
+    lk::launch_reduce(r, s);
+    LK_CUDA(ctx, cudaGetLastError());
+    return LK_OK;
+}
+
+lk_status copy_outputs(lk_ctx* ctx, Workspace& ws, int64_t n, int32_t* lk_out, double* raw_out,
+                       int32_t* status_out, cudaStream_t s) {
+    bool host = false;
+    if (lk_out) {
+        LK_CUDA(ctx, cudaMemcpyAsync(lk_out, ws.lk.p, n * sizeof(int32_t), cudaMemcpyDefault, s));
+        host |= !is_device_ptr(lk_out);
+    }
+    if (raw_out) {
+        LK_CUDA(ctx, cudaMemcpyAsync(raw_out, ws.raw.p, n * sizeof(double), cudaMemcpyDefault, s));
+        host |= !is_device_ptr(raw_out);
+    }
+    if (status_out) {
+        LK_CUDA(ctx, cudaMemcpyAsync(status_out, ws.status.p, n * sizeof(int32_t), cudaMemcpyDefault, s));
+        host |= !is_device_ptr(status_out);
+    }
+    if (host) LK_CUDA(ctx, cudaStreamSynchronize(s));
+    return LK_OK;
+}
+
+void note_stats(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStream_t s) {
+    ctx->stats = lk_stats{};
+    ctx->stats.n_pairs = (int64_t)pk.tasks.size();
+    ctx->stats.n_items = pk.n_items;
+    ctx->stats.segment_pairs = pk.segment_pairs;
+    ctx->stats.tile_rows = pk.tile_rows_max;
+    ctx->stats.tile_cols = pk.tile_cols;
+    ctx->stats_tasks = (int64_t)pk.tasks.size();
+    ctx->stats_fp64 = ws.fp64_count.p;
+    ctx->stats_overflow = ws.counters.p + 1;
+    ctx->stats_careful = reinterpret_cast<const unsigned int*>(ws.counters.p + 2);
+    ctx->stats_ev0 = (ctx->opt.timing && pk.n_items > 0) ? ws.ev0 : nullptr;
+    ctx->stats_ev1 = ws.ev1;
+    ctx->stats_stream = s;
+    ctx->stats_pending = true;
+}
+
+bool finite3(double x, double y, double z) { return std::isfinite(x) && std::isfinite(y) && std::isfinite(z); }
+
+lk_status get_pairs_on_host(lk_ctx* ctx, const int32_t* pairs, int64_t n, cudaStream_t s,
+                            std::vector<int32_t>& hp) {
+    hp.resize((size_t)(2 * n));
+    if (n == 0) return LK_OK;
+    if (is_device_ptr(pairs)) {
+        LK_CUDA(ctx, cudaMemcpyAsync(hp.data(), pairs, 2 * n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LK_CUDA(ctx, cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(hp.data(), pairs, 2 * n * sizeof(int32_t));
+    }
+    return LK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lk_default_options(lk_options* opt) {
+    if (!opt) return;
+    opt->precision = LK_MIXED;
+    opt->near_ratio = 4.0;
+    opt->int_tol = 0.1;
+    opt->mem_budget = 0;
+    opt->tile_rows = 0;
+    opt->near_capacity = 1 << 20;
+    opt->timing = 0;
+    opt->accurate_threshold = (int64_t)1 << 22;
+}
+
+const char* lk_last_error(const lk_ctx* ctx) {
+    if (ctx) return ctx->err.c_str();
+    std::lock_guard<std::mutex> g(g_err_mu);
+    return g_last_error.c_str();
+}
+
+lk_status lk_create(lk_ctx** out, const void* vertices, lk_dtype vdtype, int64_t n_vertices,
+                    const int64_t* loop_offsets, int64_t n_loops, const lk_options* opt,
+                    void* cuda_stream) {
+    if (!out) return fail(nullptr, LK_ERR_ARG, "lk_create: out is NULL");
+    *out = nullptr;
+    if (!vertices || !loop_offsets || n_vertices < 3 || n_loops < 1 ||
+        (vdtype != LK_F32 && vdtype != LK_F64))
+        return fail(nullptr, LK_ERR_ARG, "lk_create: invalid arguments");
+    lk_options o;
+    lk_default_options(&o);
+    if (opt) o = *opt;
+    if (!(o.near_ratio >= 4.0) || !(o.int_tol > 0.0 && o.int_tol < 0.5) ||
+        (o.precision != LK_MIXED && o.precision != LK_ALL_F64) || o.tile_rows < 0 ||
+        o.near_capacity < 1 || o.accurate_threshold < 0)
+        return fail(nullptr, LK_ERR_ARG, "lk_create: invalid options (near_ratio >= 4, 0 < int_tol < 0.5)");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+
+    // Host copies for validation.
+    std::vector<int64_t> off((size_t)n_loops + 1);
+    if (is_device_ptr(loop_offsets)) {
+        if (cudaMemcpy(off.data(), loop_offsets, off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(nullptr, LK_ERR_CUDA, "lk_create: cannot read loop_offsets");
+    } else {
+        std::memcpy(off.data(), loop_offsets, off.size() * sizeof(int64_t));
+    }
+    if (off[0] != 0 || off[(size_t)n_loops] != n_vertices)
+        return fail(nullptr, LK_ERR_ARG, "lk_create: loop_offsets must start at 0 and end at n_vertices");
+    for (int64_t l = 0; l < n_loops; ++l) {
+        if (off[(size_t)l + 1] - off[(size_t)l] < 3)
+            return fail(nullptr, LK_ERR_ARG, "lk_create: every loop needs at least 3 vertices");
+        if (off[(size_t)l + 1] - off[(size_t)l] > INT32_MAX)
+            return fail(nullptr, LK_ERR_ARG, "lk_create: loop too long");
+    }
+    std::vector<Vtx> hv((size_t)n_vertices);
+    {
+        const size_t esz = vdtype == LK_F32 ? 4 : 8;
+        std::vector<unsigned char> raw((size_t)n_vertices * 3 * esz);
+        if (is_device_ptr(vertices)) {
+            if (cudaMemcpy(raw.data(), vertices, raw.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return fail(nullptr, LK_ERR_CUDA, "lk_create: cannot read vertices");
+        } else {
+            std::memcpy(raw.data(), vertices, raw.size());
+        }
+        for (int64_t i = 0; i < n_vertices; ++i) {
+            double x, y, z;
+            if (vdtype == LK_F32) {
+                const float* f = reinterpret_cast<const float*>(raw.data()) + 3 * i;
+                x = f[0]; y = f[1]; z = f[2];
+            } else {
+                const double* f = reinterpret_cast<const double*>(raw.data()) + 3 * i;
+                x = f[0]; y = f[1]; z = f[2];
+            }
+            if (!finite3(x, y, z)) return fail(nullptr, LK_ERR_ARG, "lk_create: non-finite coordinate");
+            hv[(size_t)i] = Vtx{x, y, z, 0.0};
+        }
+    }
+    // Zero-length segments (Algorithm 3's input check): |s| < eps * xi, xi the
+    // mean absolute coordinate, eps the machine epsilon of the input type.
+    {
+        double xi = 0.0;
+        for (const Vtx& v : hv) xi += std::fabs(v.x) + std::fabs(v.y) + std::fabs(v.z);
+        xi /= (3.0 * (double)n_vertices);
+        const double eps = vdtype == LK_F32 ? (double)FLT_EPSILON : DBL_EPSILON;
+        const double thr = eps * xi;
+        for (int64_t l = 0; l < n_loops; ++l) {
+            const int64_t b = off[(size_t)l], e = off[(size_t)l + 1];
+            for (int64_t i = b; i < e; ++i) {
+                const Vtx& p = hv[(size_t)i];
+                const Vtx& q = hv[(size_t)(i + 1 < e ? i + 1 : b)];
+                const double len = std::sqrt((q.x - p.x) * (q.x - p.x) + (q.y - p.y) * (q.y - p.y) +
+                                             (q.z - p.z) * (q.z - p.z));
+                if (!(len >= thr) || len == 0.0) {
+                    char buf[160];
+                    snprintf(buf, sizeof buf, "lk_create: loop %lld has a zero-length segment at vertex %lld",
+                             (long long)l, (long long)(i - b));
+                    return fail(nullptr, LK_ERR_ZERO_SEGMENT, buf);
+                }
+            }
+        }
+    }
+
+    lk_ctx* ctx = new lk_ctx();
+    ctx->opt = o;
+    ctx->n_vertices = n_vertices;
+    ctx->n_loops = n_loops;
+    ctx->h_offsets = off;
+    cudaGetDevice(&ctx->device);
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    cudaError_t e = cudaMalloc(&ctx->d_V, (size_t)n_vertices * sizeof(Vtx));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_offsets, off.size() * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_aabb, (size_t)n_loops * 6 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_V, hv.data(), hv.size() * sizeof(Vtx), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_offsets, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        lk::launch_loop_aabb(ctx->d_V, ctx->d_offsets, n_loops, ctx->d_aabb, s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        const lk_status st = cuda_fail(nullptr, e, "lk_create");
+        lk_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return LK_OK;
+}
+
+lk_status lk_update(lk_ctx* ctx, const void* data, lk_dtype dtype, int is_delta, void* cuda_stream) {
+    if (!ctx) return fail(nullptr, LK_ERR_ARG, "lk_update: NULL context");
+    if (!data || (dtype != LK_F32 && dtype != LK_F64))
+        return fail(ctx, LK_ERR_ARG, "lk_update: invalid arguments");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t bytes = (size_t)ctx->n_vertices * 3 * (dtype == LK_F32 ? 4 : 8);
+    const void* src = data;
+    if (!is_device_ptr(data)) {
+        if (ctx->stage_bytes < bytes) {
+            if (ctx->d_stage) cudaFree(ctx->d_stage);
+            ctx->d_stage = nullptr;
+            ctx->stage_bytes = 0;
+            LK_CUDA(ctx, cudaMalloc(&ctx->d_stage, bytes));
+            ctx->stage_bytes = bytes;
+        }
+        LK_CUDA(ctx, cudaMemcpyAsync(ctx->d_stage, data, bytes, cudaMemcpyHostToDevice, s));
+        src = ctx->d_stage;
+    }
+    lk::launch_update(ctx->d_V, src, dtype == LK_F32 ? 0 : 1, is_delta ? 1 : 0, ctx->n_vertices, s);
+    lk::launch_loop_aabb(ctx->d_V, ctx->d_offsets, ctx->n_loops, ctx->d_aabb, s);
+    LK_CUDA(ctx, cudaGetLastError());
+    return LK_OK;
+}
+
+lk_status lk_verify(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, int32_t* lk_out,
+                    double* raw_out, int32_t* status_out, void* cuda_stream) {
+    if (!ctx) return fail(nullptr, LK_ERR_ARG, "lk_verify: NULL context");
+    if (n_pairs < 0 || (n_pairs > 0 && !loop_pairs) || n_pairs > INT32_MAX)
+        return fail(ctx, LK_ERR_ARG, "lk_verify: invalid pair list");
+    if (n_pairs == 0) return LK_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    std::vector<int32_t> hp;
+    lk_status st = get_pairs_on_host(ctx, loop_pairs, n_pairs, s, hp);
+    if (st != LK_OK) return st;
+    Packed pk;
+    if ((st = pack_pairs(ctx, hp.data(), n_pairs, pk)) != LK_OK) return st;
+    if ((st = ensure_workspace(ctx, ctx->ws, n_pairs, pk.n_items)) != LK_OK) return st;
+    if ((st = upload_packed(ctx, ctx->ws, pk, s)) != LK_OK) return st;
+    if ((st = enqueue_verify(ctx, ctx->ws, pk, s)) != LK_OK) return st;
+    note_stats(ctx, ctx->ws, pk, s);
+    return copy_outputs(ctx, ctx->ws, n_pairs, lk_out, raw_out, status_out, s);
+}
+
+lk_status lk_sync(lk_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return fail(nullptr, LK_ERR_ARG, "lk_sync: NULL context");
+    LK_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)cuda_stream));
+    return LK_OK;
+}
+
+lk_status lk_get_stats(lk_ctx* ctx, lk_stats* out) {
+    if (!ctx || !out) return fail(ctx, LK_ERR_ARG, "lk_get_stats: NULL argument");
+    if (ctx->stats_pending) {
+        LK_CUDA(ctx, cudaStreamSynchronize(ctx->stats_stream));
+        std::vector<unsigned long long> c((size_t)std::max<int64_t>(ctx->stats_tasks, 1), 0ull);
+        if (ctx->stats_tasks > 0)
+            LK_CUDA(ctx, cudaMemcpy(c.data(), ctx->stats_fp64, ctx->stats_tasks * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost));
+        unsigned long long ov = 0;
+        LK_CUDA(ctx, cudaMemcpy(&ov, ctx->stats_overflow, sizeof ov, cudaMemcpyDeviceToHost));
+        ctx->stats.fp64_pairs = (int64_t)std::accumulate(c.begin(), c.end(), 0ull);
+        ctx->stats.near_overflow = (int64_t)ov;
+        unsigned int careful = 0;
+        LK_CUDA(ctx, cudaMemcpy(&careful, ctx->stats_careful, sizeof careful, cudaMemcpyDeviceToHost));
+        ctx->stats.careful_items = careful;
+        ctx->stats.sweep_ms = -1.0;
+        if (ctx->stats_ev0) {
+            float ms = 0.0f;
+            LK_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->stats_ev0, ctx->stats_ev1));
+            ctx->stats.sweep_ms = ms;
+        }
+        ctx->stats_pending = false;
+    }
+    *out = ctx->stats;
+    return LK_OK;
+}
+
+void lk_destroy(lk_ctx* ctx) {
+    if (!ctx) return;
+    ctx->ws.release();
+    if (ctx->d_V) cudaFree(ctx->d_V);
+    if (ctx->d_offsets) cudaFree(ctx->d_offsets);
+    if (ctx->d_aabb) cudaFree(ctx->d_aabb);
+    if (ctx->d_stage) cudaFree(ctx->d_stage);
+    delete ctx;
+}
+
+lk_status lk_plan_create(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, lk_plan** out,
+                         void* cuda_stream) {
+    if (!out) return fail(ctx, LK_ERR_ARG, "lk_plan_create: out is NULL");
+    *out = nullptr;
+    if (!ctx) return fail(nullptr, LK_ERR_ARG, "lk_plan_create: NULL context");
+    if (n_pairs < 0 || (n_pairs > 0 && !loop_pairs) || n_pairs > INT32_MAX)
+        return fail(ctx, LK_ERR_ARG, "lk_plan_create: invalid pair list");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    std::vector<int32_t> hp;
+    lk_status st = get_pairs_on_host(ctx, loop_pairs, n_pairs, s, hp);
+    if (st != LK_OK) return st;
+    lk_plan* plan = new lk_plan();
+    plan->ctx = ctx;
+    if ((st = pack_pairs(ctx, hp.data(), n_pairs, plan->pk)) != LK_OK ||
+        (st = ensure_workspace(ctx, plan->ws, n_pairs, plan->pk.n_items)) != LK_OK ||
+        (st = upload_packed(ctx, plan->ws, plan->pk, s)) != LK_OK) {
+        lk_plan_destroy(plan);
+        return st;
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(plan->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        lk_plan_destroy(plan);
+        return cuda_fail(ctx, e, "lk_plan_create");
+    }
+    st = enqueue_verify(ctx, plan->ws, plan->pk, plan->capture);
+    e = cudaStreamEndCapture(plan->capture, &plan->graph);
+    if (st != LK_OK) {
+        lk_plan_destroy(plan);
+        return st;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);
+    if (e != cudaSuccess) {
+        lk_plan_destroy(plan);
+        return cuda_fail(ctx, e, "lk_plan_create: graph");
+    }
+    *out = plan;
+    return LK_OK;
+}
+
+lk_status lk_plan_run(lk_plan* plan, int32_t* lk_out, double* raw_out, int32_t* status_out,
+                      void* cuda_stream) {
+    if (!plan) return fail(nullptr, LK_ERR_ARG, "lk_plan_run: NULL plan");
+    lk_ctx* ctx = plan->ctx;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int64_t n = (int64_t)plan->pk.tasks.size();
+    if (n == 0) return LK_OK;
+    LK_CUDA(ctx, cudaGraphLaunch(plan->exec, s));
+    note_stats(ctx, plan->ws, plan->pk, s);
+    return copy_outputs(ctx, plan->ws, n, lk_out, raw_out, status_out, s);
+}
+
+void lk_plan_destroy(lk_plan* plan) {
+    if (!plan) return;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->capture) cudaStreamDestroy(plan->capture);
+    if (plan->ctx && plan->ctx->stats_fp64 == plan->ws.fp64_count.p) plan->ctx->stats_pending = false;
+    plan->ws.release();
+    delete plan;
+}
+
+}  // extern "C"

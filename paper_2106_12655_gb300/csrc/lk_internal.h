@@ -1,0 +1,110 @@
+// Internal types shared by the host runtime (lk_api.cu) and the kernels
+// (lk_kernels.cu).  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lk {
+
+// A resident vertex: FP64 coordinates padded to 32 bytes (w unused).
+struct __align__(32) Vtx {
+    double x, y, z, w;
+};
+
+// Mixed-precision tile sweep: one warp owns a work item of kTileCols columns
+// (segments i of the column loop, kLaneCols per lane) by tile_rows rows
+// (segments j of the row loop), streamed in chunks of kChunkRows rows.
+constexpr int kLaneCols = 4;
+constexpr int kTileCols = 32 * kLaneCols;
+constexpr int kChunkRows = 32;
+constexpr int kSweepWarps = 8;
+constexpr int kSweepThreads = 32 * kSweepWarps;
+
+// All-FP64 baseline sweep: one column per lane.
+constexpr int kF64TileCols = 32;
+
+// FP64 recomputes of near segment pairs are accumulated as fixed-point
+// integers of 2^-38 rad, so that their sum is independent of the order in
+// which threads add them.
+constexpr double kFixScale = 274877906944.0;  // 2^38
+
+// Per-pair flag bits.
+constexpr int kFlagIntersect = 1;
+
+// One loop pair of a verify call, laid out for the device.
+struct PairTask {
+    int64_t row_base;    // first vertex of the row loop (segments j, iterated)
+    int64_t col_base;    // first vertex of the column loop (segments i, across lanes)
+    int32_t n_rows;      // segments (= vertices) of the row loop
+    int32_t n_cols;      // segments of the column loop
+    int32_t tile_rows;   // rows per work item
+    int32_t col_tiles;   // column tiles of this pair
+    int32_t row_loop;    // loop indices, for the pair's frame
+    int32_t col_loop;
+    int32_t out_index;   // position of the pair in the caller's list
+    int32_t status;      // LK_OK, or LK_ERR_ARG for an invalid pair (then it has no items)
+    int32_t accurate;    // 1: bias-free FP32 arithmetic variant (large pairs)
+    int32_t pad;
+    double origin[3];    // staged vertex = (float)((v - origin) * scale)
+    double scale;
+};
+
+// A segment pair queued for FP64 recompute.
+struct NearEntry {
+    int32_t task;
+    int32_t j;   // segment index in the row loop
+    int32_t i;   // segment index in the column loop
+    int32_t pad;
+};
+
+struct SweepArgs {
+    const Vtx* V;                  // resident vertices, FP64
+    const PairTask* tasks;
+    const int64_t* item_begin;     // [n_tasks+1] first item of each task
+    const int32_t* item_task;      // [n_items] task of each item
+    int64_t n_items;
+    int64_t n_tasks;
+    double* partial;               // [n_items] radians: sum of (atan2 + atan2) over the item
+    unsigned long long* item_counter;
+    int64_t* careful_items;        // [n_items] items handed to the careful pass
+    unsigned int* careful_count;   // [1] entries of careful_items
+    unsigned int* careful_counter; // [1] work counter of the careful pass
+    NearEntry* near_list;
+    unsigned int* near_count;
+    int near_capacity;
+    unsigned long long* fix_acc;   // [n_tasks] fixed-point radians of FP64 recomputes
+    unsigned long long* fp64_count;// [n_tasks] segment pairs recomputed in FP64
+    unsigned long long* overflow;  // [1] recomputes evaluated in place (list full)
+    int* flags;                    // [n_tasks] kFlag* bits
+    float near_ratio_sq;           // tau^2
+};
+
+struct ReduceArgs {
+    const PairTask* tasks;
+    const int64_t* item_begin;
+    const double* partial;
+    const unsigned long long* fix_acc;
+    const int* flags;
+    int64_t n_tasks;
+    double int_tol;
+    int32_t* lk_out;               // indexed by out_index
+    double* raw_out;
+    int32_t* status_out;
+};
+
+// Kernel launchers (lk_kernels.cu).
+void launch_loop_aabb(const Vtx* V, const int64_t* offsets, int64_t n_loops, double* aabb,
+                      cudaStream_t s);
+void launch_pair_frames(PairTask* tasks, int64_t n_tasks, const double* aabb, cudaStream_t s);
+void launch_sweep_mixed(const SweepArgs& a, bool accurate, int64_t item_lo, int64_t item_hi,
+                        unsigned long long* counter, int grid, cudaStream_t s);
+void launch_sweep_f64(const SweepArgs& a, int grid, cudaStream_t s);
+void launch_sweep_careful(const SweepArgs& a, int grid, cudaStream_t s);
+void launch_near_fix(const SweepArgs& a, int grid, cudaStream_t s);
+void launch_reduce(const ReduceArgs& a, cudaStream_t s);
+void launch_update(Vtx* V, const void* data, int dtype, int is_delta, int64_t n, cudaStream_t s);
+int sweep_mixed_blocks_per_sm(bool accurate);
+int sweep_f64_blocks_per_sm();
+
+}  // namespace lk

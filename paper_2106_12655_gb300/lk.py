@@ -1,0 +1,265 @@
+"""Python binding of the C ABI in ``include/lk.h`` (argument marshalling only).
+
+Every function has the C name and forwards to ``_build/liblk.so``; all of the
+linking-number work runs in that library's CUDA kernels.  Arrays may be numpy
+arrays (host memory) or torch tensors (host or CUDA memory); pointers are
+passed through unchanged.  There is no fallback: if the library is missing,
+loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LK_OK = 0
+LK_ERR_ARG = 1
+LK_ERR_ZERO_SEGMENT = 2
+LK_ERR_INTERSECT = 3
+LK_ERR_NONINTEGER = 4
+LK_ERR_OOM = 5
+LK_ERR_TIMEOUT = 6
+LK_ERR_CUDA = 7
+LK_ERR_BUSY = 8
+LK_F32 = 0
+LK_F64 = 1
+LK_MIXED = 0
+LK_ALL_F64 = 1
+
+STATUS_NAMES = {0: "LK_OK", 1: "LK_ERR_ARG", 2: "LK_ERR_ZERO_SEGMENT", 3: "LK_ERR_INTERSECT",
+                4: "LK_ERR_NONINTEGER", 5: "LK_ERR_OOM", 6: "LK_ERR_TIMEOUT", 7: "LK_ERR_CUDA",
+                8: "LK_ERR_BUSY"}
+
+EXPORTED = ["lk_default_options", "lk_create", "lk_update", "lk_verify", "lk_sync", "lk_get_stats",
+            "lk_destroy", "lk_last_error", "lk_plan_create", "lk_plan_run", "lk_plan_destroy"]
+
+
+class lk_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("near_ratio", ctypes.c_double),
+                ("int_tol", ctypes.c_double), ("mem_budget", ctypes.c_size_t),
+                ("tile_rows", ctypes.c_int), ("near_capacity", ctypes.c_int),
+                ("timing", ctypes.c_int), ("accurate_threshold", ctypes.c_int64)]
+
+
+class lk_stats(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int64), ("n_items", ctypes.c_int64),
+                ("segment_pairs", ctypes.c_int64), ("fp64_pairs", ctypes.c_int64),
+                ("near_overflow", ctypes.c_int64), ("tile_rows", ctypes.c_int32),
+                ("tile_cols", ctypes.c_int32), ("careful_items", ctypes.c_int64),
+                ("sweep_ms", ctypes.c_double)]
+
+
+class LkError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load liblk.so (built by ``build.build()``); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("liblk.so not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i64, i32p = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p
+    lib.lk_default_options.restype = None
+    lib.lk_default_options.argtypes = [ctypes.POINTER(lk_options)]
+    lib.lk_create.restype = ctypes.c_int
+    lib.lk_create.argtypes = [ctypes.POINTER(vp), vp, ctypes.c_int, i64, vp, i64,
+                              ctypes.POINTER(lk_options), vp]
+    lib.lk_update.restype = ctypes.c_int
+    lib.lk_update.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.lk_verify.restype = ctypes.c_int
+    lib.lk_verify.argtypes = [vp, i32p, i64, vp, vp, vp, vp]
+    lib.lk_sync.restype = ctypes.c_int
+    lib.lk_sync.argtypes = [vp, vp]
+    lib.lk_get_stats.restype = ctypes.c_int
+    lib.lk_get_stats.argtypes = [vp, ctypes.POINTER(lk_stats)]
+    lib.lk_destroy.restype = None
+    lib.lk_destroy.argtypes = [vp]
+    lib.lk_last_error.restype = ctypes.c_char_p
+    lib.lk_last_error.argtypes = [vp]
+    lib.lk_plan_create.restype = ctypes.c_int
+    lib.lk_plan_create.argtypes = [vp, i32p, i64, ctypes.POINTER(vp), vp]
+    lib.lk_plan_run.restype = ctypes.c_int
+    lib.lk_plan_run.argtypes = [vp, vp, vp, vp, vp]
+    lib.lk_plan_destroy.restype = None
+    lib.lk_plan_destroy.argtypes = [vp]
+    _lib = lib
+    return lib
+
+
+# ----------------------------------------------------------------------------- marshalling
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError("expected a numpy array or torch tensor, got %r" % type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dtype_code(x):
+    dt = str(getattr(x, "dtype", ""))
+    if dt.endswith("float32"):
+        return LK_F32
+    if dt.endswith("float64"):
+        return LK_F64
+    raise TypeError("vertices must be float32 or float64, got %s" % dt)
+
+
+def _check(status, ctx=None):
+    if status != LK_OK:
+        msg = load().lk_last_error(ctx)
+        raise LkError(status, msg.decode() if msg else "")
+
+
+# ----------------------------------------------------------------------------- C functions
+
+def lk_default_options() -> lk_options:
+    o = lk_options()
+    load().lk_default_options(ctypes.byref(o))
+    return o
+
+
+def lk_create(vertices, loop_offsets, options: lk_options | None = None, stream=None):
+    """Returns the context handle (an int).  vertices [N,3] float32/float64;
+    loop_offsets int64 [L+1]."""
+    n = int(vertices.shape[0])
+    if len(vertices.shape) != 2 or vertices.shape[1] != 3:
+        raise ValueError("vertices must be [N,3]")
+    if str(loop_offsets.dtype).split(".")[-1] != "int64":
+        raise TypeError("loop_offsets must be int64")
+    out = ctypes.c_void_p()
+    st = load().lk_create(ctypes.byref(out), _ptr(vertices), _dtype_code(vertices), n,
+                          _ptr(loop_offsets), int(loop_offsets.shape[0]) - 1,
+                          ctypes.byref(options) if options is not None else None, _stream(stream))
+    _check(st)
+    return out.value
+
+
+def lk_update(ctx, data, is_delta: bool, stream=None):
+    _check(load().lk_update(ctx, _ptr(data), _dtype_code(data), 1 if is_delta else 0, _stream(stream)), ctx)
+
+
+def lk_verify(ctx, loop_pairs, lk_out=None, raw_out=None, status_out=None, stream=None):
+    """loop_pairs int32 [P,2]; outputs int32/float64/int32 [P] (host or device)."""
+    if str(loop_pairs.dtype).split(".")[-1] != "int32":
+        raise TypeError("loop_pairs must be int32")
+    n = int(loop_pairs.shape[0]) if len(loop_pairs.shape) > 0 else 0
+    _check(load().lk_verify(ctx, _ptr(loop_pairs), n, _ptr(lk_out), _ptr(raw_out), _ptr(status_out),
+                            _stream(stream)), ctx)
+
+
+def lk_sync(ctx, stream=None):
+    _check(load().lk_sync(ctx, _stream(stream)), ctx)
+
+
+def lk_get_stats(ctx) -> dict:
+    s = lk_stats()
+    _check(load().lk_get_stats(ctx, ctypes.byref(s)), ctx)
+    return {k: getattr(s, k) for k, _ in lk_stats._fields_}
+
+
+def lk_destroy(ctx):
+    if ctx:
+        load().lk_destroy(ctx)
+
+
+def lk_last_error(ctx=None) -> str:
+    m = load().lk_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def lk_plan_create(ctx, loop_pairs, stream=None):
+    if str(loop_pairs.dtype).split(".")[-1] != "int32":
+        raise TypeError("loop_pairs must be int32")
+    out = ctypes.c_void_p()
+    _check(load().lk_plan_create(ctx, _ptr(loop_pairs), int(loop_pairs.shape[0]), ctypes.byref(out),
+                                 _stream(stream)), ctx)
+    return out.value
+
+
+def lk_plan_run(plan, lk_out=None, raw_out=None, status_out=None, stream=None, ctx=None):
+    _check(load().lk_plan_run(plan, _ptr(lk_out), _ptr(raw_out), _ptr(status_out), _stream(stream)), ctx)
+
+
+def lk_plan_destroy(plan):
+    if plan:
+        load().lk_plan_destroy(plan)
+
+
+# ----------------------------------------------------------------------------- convenience
+
+class Linker:
+    """Owns one context; ``verify(pairs)`` returns (lk, raw, status) numpy arrays."""
+
+    def __init__(self, vertices, loop_offsets, precision=LK_MIXED, stream=None, **opts):
+        o = lk_default_options()
+        o.precision = precision
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.stream = stream
+        self.ctx = lk_create(vertices, loop_offsets, o, stream)
+
+    def verify(self, pairs):
+        pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        n = pairs.shape[0]
+        lk = np.zeros(n, np.int32)
+        raw = np.zeros(n, np.float64)
+        st = np.zeros(n, np.int32)
+        lk_verify(self.ctx, pairs, lk, raw, st, self.stream)
+        return lk, raw, st
+
+    def update(self, data, is_delta=True):
+        lk_update(self.ctx, data, is_delta, self.stream)
+
+    def stats(self):
+        return lk_get_stats(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            lk_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

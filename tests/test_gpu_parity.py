@@ -1,0 +1,295 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bar (per pair): the rounded linking number bit-exact, the raw sum within
+1e-6 of the oracle's FP64 sum (the tolerance stated for this method) and
+within int_tol = 0.1 of an integer, status LK_OK.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2106_12655_gb300 import lk
+from paper_2106_12655_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RAW_TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_12655_gb300 import build as B
+
+    B.build()
+    lk.load()
+
+
+def run(g, pairs=None, precision=lk.LK_MIXED, on_device=True, stats=False, **opts):
+    pairs = g.pairs if pairs is None else np.asarray(pairs, np.int32).reshape(-1, 2)
+    o = lk.lk_default_options()
+    o.precision = precision
+    for k, v in opts.items():
+        setattr(o, k, v)
+    stream = torch.cuda.current_stream()
+    if on_device:
+        v = torch.from_numpy(np.ascontiguousarray(g.vertices)).cuda()
+        off = torch.from_numpy(g.offsets).cuda()
+        pr = torch.from_numpy(np.ascontiguousarray(pairs)).cuda()
+    else:
+        v, off, pr = np.ascontiguousarray(g.vertices), g.offsets, np.ascontiguousarray(pairs)
+    n = pairs.shape[0]
+    ctx = lk.lk_create(v, off, o, stream)
+    try:
+        if on_device:
+            lk_o = torch.zeros(n, dtype=torch.int32, device="cuda")
+            raw = torch.zeros(n, dtype=torch.float64, device="cuda")
+            st = torch.zeros(n, dtype=torch.int32, device="cuda")
+            lk.lk_verify(ctx, pr, lk_o, raw, st, stream)
+            lk.lk_sync(ctx, stream)
+            res = lk_o.cpu().numpy(), raw.cpu().numpy(), st.cpu().numpy()
+        else:
+            lk_o, raw, st = np.zeros(n, np.int32), np.zeros(n), np.zeros(n, np.int32)
+            lk.lk_verify(ctx, pr, lk_o, raw, st, stream)
+            res = lk_o, raw, st
+        s = lk.lk_get_stats(ctx)
+    finally:
+        lk.lk_destroy(ctx)
+    return res + (s,) if stats else res
+
+
+def check_against_oracle(g, pairs=None, tol=RAW_TOL, **kw):
+    pairs = g.pairs if pairs is None else np.asarray(pairs, np.int32).reshape(-1, 2)
+    lk_o, raw, st = run(g, pairs, **kw)
+    ref = O.link_pairs(g.vertices, g.offsets, pairs)
+    ref_lk = O.round_lk(ref)
+    assert np.all(st == lk.LK_OK), np.unique(st, return_counts=True)
+    assert np.array_equal(lk_o, ref_lk.astype(np.int32)), np.nonzero(lk_o != ref_lk)
+    err = np.abs(raw - ref)
+    assert err.max() <= tol, (err.max(), int(err.argmax()))
+    assert np.abs(raw - lk_o).max() <= 0.1
+    return raw, ref
+
+
+# ----------------------------------------------------------------------------- configs
+
+def test_ring_chain_all_pairs():
+    g = W.ring_chain()
+    raw, ref = check_against_oracle(g)
+    assert sorted(set(O.round_lk(ref).tolist())) == [-1, 0, 1]
+
+
+def test_ring_chain_all_f64_baseline():
+    check_against_oracle(W.ring_chain(), precision=lk.LK_ALL_F64, tol=1e-9)
+
+
+def test_chainmail_sheet_full_size():
+    """The benchmarked workload: 2,048 rings x 256 segments, all AABB candidates."""
+    g = W.chainmail()
+    raw, ref = check_against_oracle(g)
+    counts = np.unique(O.round_lk(ref), return_counts=True)
+    assert set(counts[0].tolist()) == {-1, 0, 1}
+
+
+def test_chainmail_sheet_accurate_variant():
+    check_against_oracle(W.chainmail(), accurate_threshold=0)
+
+
+def test_chainmail_plan_graph_matches_oracle():
+    g = W.chainmail()
+    v = torch.from_numpy(g.vertices).cuda()
+    off = torch.from_numpy(g.offsets).cuda()
+    pr = torch.from_numpy(g.pairs).cuda()
+    n = g.pairs.shape[0]
+    stream = torch.cuda.current_stream()
+    ctx = lk.lk_create(v, off, None, stream)
+    plan = lk.lk_plan_create(ctx, pr, stream)
+    try:
+        outs = []
+        for _ in range(2):
+            lk_o = torch.zeros(n, dtype=torch.int32, device="cuda")
+            raw = torch.zeros(n, dtype=torch.float64, device="cuda")
+            st = torch.zeros(n, dtype=torch.int32, device="cuda")
+            lk.lk_plan_run(plan, lk_o, raw, st, stream, ctx=ctx)
+            torch.cuda.synchronize()
+            outs.append((lk_o.cpu().numpy(), raw.cpu().numpy(), st.cpu().numpy()))
+    finally:
+        lk.lk_plan_destroy(plan)
+        lk.lk_destroy(ctx)
+    ref = O.link_pairs(g.vertices, g.offsets, g.pairs)
+    for lk_o, raw, st in outs:
+        assert np.all(st == 0)
+        assert np.array_equal(lk_o, O.round_lk(ref).astype(np.int32))
+        assert np.abs(raw - ref).max() <= RAW_TOL
+    assert np.array_equal(outs[0][1], outs[1][1])      # graph replays are bit-identical
+
+
+def test_knit_yarn_sampled_pairs():
+    """600 loops of 1k-20k segments: every pair on the GPU, a seeded sample of
+    pairs (spanning the size range) against the oracle, every pair integral."""
+    g = W.knit_yarn()
+    lk_o, raw, st = run(g)
+    assert np.all(st == 0)
+    assert np.abs(raw - lk_o).max() < 1e-4
+    sizes = g.sizes()[g.pairs].prod(axis=1)
+    order = np.argsort(sizes)
+    rng = np.random.default_rng(7)
+    pick = np.unique(np.concatenate([order[:4], order[-3:], rng.choice(len(order), 9, replace=False)]))
+    ref = O.link_pairs(g.vertices, g.offsets, g.pairs[pick])
+    assert np.array_equal(lk_o[pick], O.round_lk(ref).astype(np.int32))
+    assert np.abs(raw[pick] - ref).max() <= RAW_TOL
+    assert set(np.unique(lk_o).tolist()) <= {-1, 0, 1}
+
+
+@pytest.mark.parametrize("p,q,n", [(2, 3, 250_000), (31, 37, 1_000_000)])
+def test_torus_link_closed_form_large(p, q, n):
+    """Single huge pairs (intra-pair split): the exact sum is -p*q for this
+    orientation; the raw sum must be within 1e-6 of it."""
+    g = W.torus_link(p, q, n, dtype=np.float32)
+    lk_o, raw, st = run(g)
+    assert st[0] == 0
+    assert abs(lk_o[0]) == p * q
+    assert abs(raw[0] - lk_o[0]) <= RAW_TOL
+
+
+def test_torus_link_small_matches_oracle_f32_and_f64_inputs():
+    for dt in (np.float32, np.float64):
+        g = W.torus_link(5, 7, 3000, dtype=dt, n2=2711)
+        check_against_oracle(g)
+
+
+# ----------------------------------------------------------------------------- tiles and edges
+
+@pytest.mark.parametrize("n1,n2", [(3, 3), (3, 4), (4, 5), (5, 129), (127, 128), (128, 129),
+                                   (129, 255), (256, 257), (300, 1000)])
+def test_tile_edges_random_polygons(n1, n2):
+    rng = np.random.default_rng(n1 * 1000 + n2)
+    loops = []
+    for n in (n1, n2):
+        t = np.sort(rng.uniform(0, 2 * np.pi, n))
+        r = 1.0 + 0.2 * rng.normal(size=(n, 1))
+        c = rng.normal(scale=0.3, size=3)
+        loops.append(c + r * np.stack([np.cos(t), np.sin(t), 0.3 * rng.normal(size=n)], 1))
+    loops[1] = loops[1][:, [0, 2, 1]] + np.array([1.0, 0.0, 0.0])
+    g = W.from_loops(loops, pairs=[[0, 1], [1, 0]])
+    for tile_rows in (0, 32, 64, 96):
+        for accurate_threshold in (0, 1 << 62):          # both FP32 arithmetic variants
+            check_against_oracle(g, tile_rows=tile_rows, accurate_threshold=accurate_threshold)
+
+
+def test_random_integer_polygons_against_exact_crossings():
+    from crossings import linking_number_exact
+
+    rng = np.random.default_rng(12)
+    loops, pairs, expect = [], [], []
+    while len(pairs) < 40:
+        n1, n2 = rng.integers(4, 40, 2)
+        l = rng.integers(-40, 41, (n1, 3))
+        k = rng.integers(-40, 41, (n2, 3))
+        try:
+            cc = linking_number_exact(l, k, rng)
+        except Exception:
+            continue
+        pairs.append([len(loops), len(loops) + 1])
+        loops += [l.astype(np.float64), k.astype(np.float64)]
+        expect.append(cc)
+    g = W.from_loops(loops, pairs=pairs)
+    lk_o, raw, st = run(g)
+    assert np.all(st == 0), st
+    assert np.array_equal(lk_o, np.asarray(expect, np.int32))
+    ref = O.link_pairs(g.vertices, g.offsets, g.pairs)
+    assert np.abs(raw - ref).max() <= RAW_TOL
+
+
+def test_near_segments_take_the_fp64_path():
+    """Two loops with segments within a segment length of each other: the
+    careful pass must send those pairs to FP64 and still match the oracle."""
+    t = np.arange(400) * 2 * np.pi / 400
+    a = np.stack([np.cos(t), np.sin(t), 0 * t], 1)
+    # b threads a's disk and passes 0.004 outside a at (1.004, 0, 0); a's
+    # segments are ~0.0157 long, b's ~0.0079
+    b = np.stack([0.5 + 0.504 * np.cos(t + 0.01), 0 * t, 0.504 * np.sin(t + 0.01)], 1)
+    g = W.from_loops([a, b], pairs=[[0, 1]])
+    lk_o, raw, st, s = run(g, stats=True)
+    ref = O.link_pairs(g.vertices, g.offsets, g.pairs)
+    assert st[0] == 0 and lk_o[0] == O.round_lk(ref)[0]
+    assert abs(raw[0] - ref[0]) <= RAW_TOL
+    assert s["fp64_pairs"] > 0
+    # a tiny list forces the in-place FP64 evaluation of the overflow
+    lk2, raw2, st2, s2 = run(g, stats=True, near_capacity=3)
+    assert s2["near_overflow"] > 0
+    assert st2[0] == 0 and lk2[0] == lk_o[0] and abs(raw2[0] - ref[0]) <= RAW_TOL
+
+
+def test_intersecting_loops_are_reported():
+    t = np.arange(64) * 2 * np.pi / 64
+    a = np.stack([np.cos(t), np.sin(t), 0 * t], 1)
+    b = np.stack([np.cos(t), 0 * t, np.sin(t)], 1)          # shares vertices (+-1,0,0) with a
+    c = np.stack([5 + np.cos(t), np.sin(t), 0 * t], 1)
+    g = W.from_loops([a, b, c], pairs=[[0, 1], [0, 2]])
+    for prec in (lk.LK_MIXED, lk.LK_ALL_F64):
+        lk_o, raw, st = run(g, precision=prec)
+        assert st[0] == lk.LK_ERR_INTERSECT and lk_o[0] == 0
+        assert st[1] == lk.LK_OK and lk_o[1] == 0
+
+
+def test_invalid_pairs_only_affect_themselves():
+    g = W.ring_chain()
+    pairs = np.array([[0, 1], [3, 3], [0, 99], [-1, 2], [2, 3]], np.int32)
+    lk_o, raw, st = run(g, pairs)
+    assert st.tolist() == [0, lk.LK_ERR_ARG, lk.LK_ERR_ARG, lk.LK_ERR_ARG, 0]
+    ref = O.link_pairs(g.vertices, g.offsets, pairs[[0, 4]])
+    assert np.abs(raw[[0, 4]] - ref).max() <= RAW_TOL
+
+
+def test_empty_pair_list():
+    g = W.ring_chain()
+    lk_o, raw, st = run(g, np.zeros((0, 2), np.int32), on_device=False)
+    assert lk_o.shape == (0,)
+
+
+def test_host_and_device_buffers_agree():
+    g = W.ring_chain()
+    a = run(g, on_device=True)
+    b = run(g, on_device=False)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_result_independent_of_batch_and_rerun():
+    g = W.chainmail(rows=6, cols=10)
+    full = run(g)[1]
+    again = run(g)[1]
+    assert np.array_equal(full, again)
+    rng = np.random.default_rng(3)
+    pick = rng.choice(g.pairs.shape[0], 7, replace=False)
+    for k in pick:
+        alone = run(g, g.pairs[k:k + 1])[1]
+        assert alone[0] == full[k]
+    shuffled = rng.permutation(g.pairs.shape[0])
+    assert np.array_equal(run(g, g.pairs[shuffled])[1], full[shuffled])
+
+
+def test_update_matches_fresh_context():
+    g = W.chainmail(rows=6, cols=10, dtype=np.float32)
+    rng = np.random.default_rng(5)
+    delta = rng.normal(scale=1e-3, size=g.vertices.shape).astype(np.float32)
+    stream = torch.cuda.current_stream()
+    v = torch.from_numpy(g.vertices).cuda()
+    off = torch.from_numpy(g.offsets).cuda()
+    n = g.pairs.shape[0]
+    ctx = lk.lk_create(v, off, None, stream)
+    try:
+        lk.lk_update(ctx, torch.from_numpy(delta).cuda(), True, stream)
+        lk_o, raw, st = np.zeros(n, np.int32), np.zeros(n), np.zeros(n, np.int32)
+        lk.lk_verify(ctx, g.pairs, lk_o, raw, st, stream)
+    finally:
+        lk.lk_destroy(ctx)
+    moved = W.Geometry((g.vertices.astype(np.float64) + delta.astype(np.float64)), g.offsets, g.pairs)
+    fresh = run(moved)
+    assert np.array_equal(lk_o, fresh[0])
+    assert np.abs(raw - fresh[1]).max() <= 1e-9
+    ref = O.link_pairs(moved.vertices, moved.offsets, moved.pairs)
+    assert np.abs(raw - ref).max() <= RAW_TOL
