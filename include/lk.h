@@ -176,6 +176,38 @@ lk_status lk_plan_run(lk_plan* plan, int32_t* lk_out, double* raw_out, int32_t* 
                       void* cuda_stream);
 void lk_plan_destroy(lk_plan* plan);
 
+/*
+ * Allocation-free verify (the paper has no counterpart; this is a service of
+ * this library).  For callers that cannot allocate device memory at the time
+ * they verify: a simulation step under a strict no-allocation rule (a device
+ * allocation synchronises the GPU and can stall a real-time loop), a process
+ * whose memory pool already owns all of device memory, or a host program that
+ * forbids libraries to call cudaMalloc.  It runs the same kernels as
+ * lk_verify with the default options, but every work buffer lives in one
+ * file-scope device array of 32 MiB that each GPU loading the library holds
+ * until the process exits; it calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *  vertices     : [n_vertices][3] of vdtype, host or device memory.
+ *  loop_offsets : [n_loops+1] int64, HOST memory (CSR as for lk_create).
+ *  loop_pairs   : [n_pairs][2] int32, HOST memory.
+ *  lk_out, raw_out, status_out : as for lk_verify (host or device, may be NULL).
+ * Limits: n_vertices <= 262144, n_loops <= 16384, n_pairs <= 16384 and at most
+ * 262144 work items (tiles of 128 x tile_rows segment pairs); larger inputs
+ * return LK_ERR_ARG with a message naming the limit, before any device work.
+ * The first call on each device looks up the array's device address once
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the one array and leaves its contents behind
+ * (each call clears what must start at zero), so calls whose work overlaps on
+ * the GPU -- on different streams, or from different host threads -- race and
+ * must be serialised by the caller.  The input checks of lk_create (finite
+ * coordinates, zero-length segments) are not made; degenerate geometry shows
+ * up as per-pair LK_ERR_INTERSECT or LK_ERR_NONINTEGER.
+ */
+lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, int64_t n_vertices,
+                            const int64_t* loop_offsets, int64_t n_loops,
+                            const int32_t* loop_pairs, int64_t n_pairs, int32_t* lk_out,
+                            double* raw_out, int32_t* status_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

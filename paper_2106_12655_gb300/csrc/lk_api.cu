@@ -703,3 +703,168 @@ void lk_plan_destroy(lk_plan* plan) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Allocation-free verify.
+//
+// Some callers cannot allocate device memory when they need a linking-number
+// check: a simulation step that runs under a strict no-allocation rule (a
+// device allocation synchronises the GPU and can stall a real-time loop),
+// a process whose memory pool already owns all of device memory, or a host
+// program that manages memory itself and forbids libraries to call
+// cudaMalloc.  lk_verify_noalloc serves them: it runs the same kernels as
+// lk_verify, but every work buffer -- the converted geometry, loop boxes,
+// pair tasks, item tables, partial sums, recompute list, counters and
+// results -- lives in one file-scope device array of fixed size.  It calls
+// no cudaMalloc, cudaFree or allocating library routine.
+namespace {
+
+constexpr size_t kNoallocScratchBytes = (size_t)32 << 20;   // 32 MiB per device, held until exit
+constexpr int64_t kNoallocMaxVertices = (int64_t)1 << 18;
+constexpr int64_t kNoallocMaxLoops = (int64_t)1 << 14;
+constexpr int64_t kNoallocMaxPairs = (int64_t)1 << 14;
+constexpr int64_t kNoallocMaxItems = (int64_t)1 << 18;
+constexpr int kNoallocNearCapacity = 1 << 16;
+constexpr int kNoallocMaxDevices = 64;
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+}  // namespace
+
+// Shared by every call on a device: contents persist between calls.
+static __device__ __align__(256) unsigned char lk_noalloc_scratch[kNoallocScratchBytes];
+
+namespace {
+
+// Carve the scratch into the buffers of one verify at the fixed maxima.
+struct NoallocLayout {
+    size_t off = 0;
+    unsigned char* base;
+    explicit NoallocLayout(void* b) : base((unsigned char*)b) {}
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// Address of the scratch array on the current device, looked up once per
+// device (in host code the array's name is not a device address).
+lk_status noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "lk_verify_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kNoallocMaxDevices)
+        return fail(nullptr, LK_ERR_ARG, "lk_verify_noalloc: device index out of range");
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, lk_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return cuda_fail(nullptr, e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                             "lk_verify_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return LK_OK;
+}
+
+}  // namespace
+
+extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, int64_t n_vertices,
+                                       const int64_t* loop_offsets, int64_t n_loops,
+                                       const int32_t* loop_pairs, int64_t n_pairs, int32_t* lk_out,
+                                       double* raw_out, int32_t* status_out, void* cuda_stream) {
+    char msg[200];
+    if (!vertices || !loop_offsets || (n_pairs > 0 && !loop_pairs) || n_vertices < 3 || n_loops < 1 ||
+        n_pairs < 0 || (vdtype != LK_F32 && vdtype != LK_F64))
+        return fail(nullptr, LK_ERR_ARG, "lk_verify_noalloc: invalid arguments");
+    if (n_vertices > kNoallocMaxVertices || n_loops > kNoallocMaxLoops || n_pairs > kNoallocMaxPairs) {
+        snprintf(msg, sizeof msg,
+                 "lk_verify_noalloc: size beyond the static scratch limits (vertices <= %lld, loops <= %lld, "
+                 "pairs <= %lld)", (long long)kNoallocMaxVertices, (long long)kNoallocMaxLoops,
+                 (long long)kNoallocMaxPairs);
+        return fail(nullptr, LK_ERR_ARG, msg);
+    }
+    if (is_device_ptr(loop_offsets) || (n_pairs > 0 && is_device_ptr(loop_pairs)))
+        return fail(nullptr, LK_ERR_ARG, "lk_verify_noalloc: loop_offsets and loop_pairs must be host memory");
+    if (loop_offsets[0] != 0 || loop_offsets[n_loops] != n_vertices)
+        return fail(nullptr, LK_ERR_ARG, "lk_verify_noalloc: loop_offsets must start at 0 and end at n_vertices");
+    for (int64_t l = 0; l < n_loops; ++l)
+        if (loop_offsets[l + 1] - loop_offsets[l] < 3)
+            return fail(nullptr, LK_ERR_ARG, "lk_verify_noalloc: every loop needs at least 3 vertices");
+    if (n_pairs == 0) return LK_OK;
+
+    void* scratch = nullptr;
+    lk_status st = noalloc_scratch(&scratch);
+    if (st != LK_OK) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+
+    // A context on the stack pointing into the scratch; it owns nothing and is
+    // never passed to lk_destroy.
+    lk_ctx ctx;
+    lk_default_options(&ctx.opt);
+    ctx.opt.near_capacity = kNoallocNearCapacity;
+    ctx.n_vertices = n_vertices;
+    ctx.n_loops = n_loops;
+    ctx.h_offsets.assign(loop_offsets, loop_offsets + n_loops + 1);
+    cudaGetDevice(&ctx.device);
+    cudaDeviceGetAttribute(&ctx.num_sms, cudaDevAttrMultiProcessorCount, ctx.device);
+
+    NoallocLayout L(scratch);
+    ctx.d_V = L.take<Vtx>((size_t)kNoallocMaxVertices);
+    double* raw_in = L.take<double>((size_t)kNoallocMaxVertices * 3);   // host vertices staged here
+    ctx.d_offsets = L.take<int64_t>((size_t)kNoallocMaxLoops + 1);
+    ctx.d_aabb = L.take<double>((size_t)kNoallocMaxLoops * 6);
+    Workspace ws;
+    auto bind = [&](auto& buf, size_t count) {
+        using T = typename std::remove_pointer<decltype(buf.p)>::type;
+        buf.p = L.take<T>(count);
+        buf.cap = count;
+    };
+    bind(ws.tasks, (size_t)kNoallocMaxPairs);
+    bind(ws.item_begin, (size_t)kNoallocMaxPairs + 1);
+    bind(ws.item_task, (size_t)kNoallocMaxItems);
+    bind(ws.partial, (size_t)kNoallocMaxItems);
+    bind(ws.careful_items, (size_t)kNoallocMaxItems);
+    bind(ws.near_list, (size_t)kNoallocNearCapacity);
+    bind(ws.fix_acc, (size_t)kNoallocMaxPairs);
+    bind(ws.fp64_count, (size_t)kNoallocMaxPairs);
+    bind(ws.flags, (size_t)kNoallocMaxPairs);
+    bind(ws.counters, 8);
+    bind(ws.lk, (size_t)kNoallocMaxPairs);
+    bind(ws.raw, (size_t)kNoallocMaxPairs);
+    bind(ws.status, (size_t)kNoallocMaxPairs);
+    if (L.off > kNoallocScratchBytes) return fail(nullptr, LK_ERR_ARG, "lk_verify_noalloc: scratch layout overflow");
+
+    Packed pk;
+    if ((st = pack_pairs(&ctx, loop_pairs, n_pairs, pk)) != LK_OK) return fail(nullptr, st, ctx.err);
+    if (pk.n_items > kNoallocMaxItems) {
+        snprintf(msg, sizeof msg, "lk_verify_noalloc: %lld work items exceed the static limit of %lld",
+                 (long long)pk.n_items, (long long)kNoallocMaxItems);
+        return fail(nullptr, LK_ERR_ARG, msg);
+    }
+    // Geometry into the scratch: the vertices as resident FP64 (the existing
+    // replace-vertices kernel converts from the caller's layout), offsets,
+    // loop boxes.
+    const size_t vbytes = (size_t)n_vertices * 3 * (vdtype == LK_F32 ? 4 : 8);
+    const void* vsrc = vertices;
+    if (!is_device_ptr(vertices)) {
+        cudaError_t e = cudaMemcpyAsync(raw_in, vertices, vbytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "lk_verify_noalloc: vertices");
+        vsrc = raw_in;
+    }
+    cudaError_t e = cudaMemcpyAsync(ctx.d_offsets, loop_offsets, (size_t)(n_loops + 1) * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "lk_verify_noalloc: offsets");
+    lk::launch_update(ctx.d_V, vsrc, vdtype == LK_F32 ? 0 : 1, 0, n_vertices, s);
+    lk::launch_loop_aabb(ctx.d_V, ctx.d_offsets, n_loops, ctx.d_aabb, s);
+    if ((st = ensure_workspace(&ctx, ws, n_pairs, pk.n_items)) != LK_OK ||
+        (st = upload_packed(&ctx, ws, pk, s)) != LK_OK || (st = enqueue_verify(&ctx, ws, pk, s)) != LK_OK ||
+        (st = copy_outputs(&ctx, ws, n_pairs, lk_out, raw_out, status_out, s)) != LK_OK)
+        return fail(nullptr, st, ctx.err);
+    return LK_OK;
+}

@@ -34,7 +34,8 @@ STATUS_NAMES = {0: "LK_OK", 1: "LK_ERR_ARG", 2: "LK_ERR_ZERO_SEGMENT", 3: "LK_ER
                 8: "LK_ERR_BUSY"}
 
 EXPORTED = ["lk_default_options", "lk_create", "lk_update", "lk_verify", "lk_sync", "lk_get_stats",
-            "lk_destroy", "lk_last_error", "lk_plan_create", "lk_plan_run", "lk_plan_destroy"]
+            "lk_destroy", "lk_last_error", "lk_plan_create", "lk_plan_run", "lk_plan_destroy",
+            "lk_verify_noalloc"]
 
 
 class lk_options(ctypes.Structure):
@@ -98,6 +99,8 @@ def load(path: str | None = None):
     lib.lk_plan_run.argtypes = [vp, vp, vp, vp, vp]
     lib.lk_plan_destroy.restype = None
     lib.lk_plan_destroy.argtypes = [vp]
+    lib.lk_verify_noalloc.restype = ctypes.c_int
+    lib.lk_verify_noalloc.argtypes = [vp, ctypes.c_int, i64, vp, i64, i32p, i64, vp, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -217,6 +220,20 @@ def lk_plan_run(plan, lk_out=None, raw_out=None, status_out=None, stream=None, c
 def lk_plan_destroy(plan):
     if plan:
         load().lk_plan_destroy(plan)
+
+
+def lk_verify_noalloc(vertices, loop_offsets, loop_pairs, lk_out=None, raw_out=None, status_out=None,
+                      stream=None):
+    """Allocation-free verify: all work buffers in the library's static device
+    array.  loop_offsets (int64) and loop_pairs (int32) must be host arrays."""
+    if str(loop_pairs.dtype).split(".")[-1] != "int32":
+        raise TypeError("loop_pairs must be int32")
+    if str(loop_offsets.dtype).split(".")[-1] != "int64":
+        raise TypeError("loop_offsets must be int64")
+    _check(load().lk_verify_noalloc(_ptr(vertices), _dtype_code(vertices), int(vertices.shape[0]),
+                                    _ptr(loop_offsets), int(loop_offsets.shape[0]) - 1, _ptr(loop_pairs),
+                                    int(loop_pairs.shape[0]), _ptr(lk_out), _ptr(raw_out), _ptr(status_out),
+                                    _stream(stream)))
 
 
 # ----------------------------------------------------------------------------- convenience
