@@ -177,6 +177,63 @@ lk_status lk_plan_run(lk_plan* plan, int32_t* lk_out, double* raw_out, int32_t* 
 void lk_plan_destroy(lk_plan* plan);
 
 /*
+ * Serving: continuous batching of verify requests over resident geometry
+ * (the per-frame verification of Sec. 5's simulation examples, as a service).
+ * A server owns a device arena of arena_bytes (requests are admitted only
+ * while their work buffers fit in it), a pinned host arena of host_bytes for
+ * results, and a FIFO of submitted requests.  lk_server_step retires finished
+ * waves, admits queued requests while fewer than max_requests are admitted and
+ * the arena has room, then launches one wave: a single persistent launch over
+ * up to wave_items work items taken, in admission order, from every admitted
+ * request with items left -- so a request that arrives while others run shares
+ * the device with them.  A request's result does not depend on what shares
+ * its waves (each pair's tiling and reduction order depend only on the pair).
+ * All work of a server runs on its own stream (lk_server_stream); the caller
+ * must not change (lk_update) a context while it has unfinished requests, or
+ * must order the update on that stream after they finish.
+ */
+typedef struct lk_server_options {
+    int max_requests;     /* requests admitted at once (default 64) */
+    size_t arena_bytes;   /* device memory for request work buffers (default 1 GiB) */
+    size_t host_bytes;    /* pinned host memory for results (default 64 MiB) */
+    int64_t wave_items;   /* work items per wave (default 16384) */
+    int near_capacity;    /* FP64 recompute list entries per request (default 4096) */
+    int max_queue;        /* queued requests before submit returns LK_ERR_BUSY (default 65536) */
+} lk_server_options;
+
+typedef struct lk_server_stats {
+    int64_t submitted, admitted, completed;
+    int64_t queued, running;             /* now */
+    int64_t waves, waves_in_flight;
+    int64_t items_launched;
+    int64_t max_requests_per_wave;       /* most requests that shared one wave */
+    int64_t arena_used;                  /* bytes of the device arena in use now */
+} lk_server_stats;
+
+void lk_server_default_options(lk_server_options* opt);
+/* Errors: LK_ERR_ARG, LK_ERR_OOM (arena allocation), LK_ERR_CUDA. */
+lk_status lk_server_create(lk_server** out, const lk_server_options* opt);
+/* The server's CUDA stream (cudaStream_t). */
+void* lk_server_stream(lk_server* srv);
+/* Queue a request to verify n_pairs >= 1 pairs of ctx (host or device memory,
+ * copied).  *ticket identifies it.  Errors: LK_ERR_ARG; LK_ERR_BUSY (queue
+ * full); LK_ERR_OOM (the request alone exceeds the arena). */
+lk_status lk_server_submit(lk_server* srv, lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs,
+                           int64_t* ticket);
+/* Retire finished waves, admit, launch the next wave.  wait = 1 also blocks
+ * until the oldest wave in flight has finished. */
+lk_status lk_server_step(lk_server* srv, int wait);
+/* *done = 1 and the results copied to the host buffers ([n_pairs] each, may
+ * be NULL) once the request has finished; the ticket is then released.
+ * *done = 0 while it is queued or running. */
+lk_status lk_server_poll(lk_server* srv, int64_t ticket, int* done, int32_t* lk_out, double* raw_out,
+                         int32_t* status_out);
+lk_status lk_server_get_stats(lk_server* srv, lk_server_stats* out);
+const char* lk_server_last_error(const lk_server* srv);
+/* Waits for the server's stream, then frees everything it owns. */
+void lk_server_destroy(lk_server* srv);
+
+/*
  * Allocation-free verify (the paper has no counterpart; this is a service of
  * this library).  For callers that cannot allocate device memory at the time
  * they verify: a simulation step under a strict no-allocation rule (a device

@@ -16,7 +16,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <mutex>
+#include <type_traits>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -208,6 +211,7 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
         const int64_t na = ctx->h_offsets[a + 1] - ctx->h_offsets[a];
         const int64_t nb = ctx->h_offsets[b + 1] - ctx->h_offsets[b];
         const bool a_rows = na >= nb;
+        t.V = ctx->d_V;
         t.row_loop = a_rows ? a : b;
         t.col_loop = a_rows ? b : a;
         t.row_base = ctx->h_offsets[t.row_loop];
@@ -297,7 +301,6 @@ lk_status upload_packed(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStream
 
 lk::SweepArgs sweep_args(const lk_ctx* ctx, Workspace& ws, const Packed& pk) {
     lk::SweepArgs a{};
-    a.V = ctx->d_V;
     a.tasks = ws.tasks.p;
     a.item_begin = ws.item_begin.p;
     a.item_task = ws.item_task.p;
@@ -868,3 +871,486 @@ extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, in
         return fail(nullptr, st, ctx.err);
     return LK_OK;
 }
+
+// ----------------------------------------------------------------------------
+// Serving: continuous batching of verify requests.
+//
+// A server owns a device arena (the memory budget that admission checks), a
+// pinned host arena for results, and a FIFO of submitted requests.  Each
+// lk_server_step retires waves that have finished, admits queued requests
+// while request slots and arena space allow, and launches one wave: a
+// persistent launch over up to wave_items work items taken in admission order
+// from every admitted request that still has items, so that requests which
+// arrived while others were running share the device with them.  A request
+// whose last items are in a wave gets its careful pass, FP64 recomputes and
+// reduction right after that wave; its results are copied to pinned memory
+// and handed out by lk_server_poll.
+namespace {
+
+// First-fit allocator over byte offsets [0, size), 256-byte granules.
+struct Arena {
+    size_t size = 0;
+    std::map<size_t, size_t> free_;   // offset -> length
+    size_t used = 0;
+
+    void init(size_t n) {
+        size = n;
+        free_.clear();
+        if (n) free_[0] = n;
+        used = 0;
+    }
+    static size_t round(size_t n) { return (std::max<size_t>(n, 1) + 255) & ~(size_t)255; }
+    bool alloc(size_t n, size_t* off) {
+        n = round(n);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            *off = it->first;
+            const size_t rest = it->second - n, at = it->first + n;
+            free_.erase(it);
+            if (rest) free_[at] = rest;
+            used += n;
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        n = round(n);
+        used -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+enum ReqState { kQueued = 0, kRunning = 1, kLaunched = 2, kDone = 3 };
+
+struct Request {
+    int64_t ticket = 0;
+    lk_ctx* ctx = nullptr;
+    std::vector<int32_t> pairs;
+    Packed pk;
+    bool packed = false;
+    Workspace ws;              // pointers into the device arena
+    size_t dev_off = 0, dev_bytes = 0;
+    size_t host_off = 0, host_bytes = 0;
+    int32_t* h_lk = nullptr;   // pinned results
+    double* h_raw = nullptr;
+    int32_t* h_status = nullptr;
+    lk::SweepArgs args{};
+    int64_t next_item = 0;
+    int state = kQueued;
+};
+
+struct Wave {
+    cudaEvent_t done = nullptr;
+    int slot = 0;
+    std::vector<Request*> completing;
+};
+
+constexpr int kWaveSlots = 3;          // waves in flight at most
+constexpr int kMaxSegs = 256;          // request runs per wave
+
+// Carve one request's work buffers out of the arena at `base` (or, with
+// base = 0, only measure them); returns the bytes used.
+size_t request_layout(const Packed& pk, int near_cap, Workspace* ws, uintptr_t base) {
+    size_t off = 0;
+    const size_t P = std::max<size_t>(pk.tasks.size(), 1), I = (size_t)std::max<int64_t>(pk.n_items, 1);
+    auto bind = [&](auto& buf, size_t count) {
+        using T = typename std::remove_pointer<decltype(buf.p)>::type;
+        off = (off + 255) & ~(size_t)255;
+        buf.p = reinterpret_cast<T*>(base + off);
+        buf.cap = count;
+        off += count * sizeof(T);
+    };
+    bind(ws->tasks, P);
+    bind(ws->item_begin, P + 1);
+    bind(ws->item_task, I);
+    bind(ws->partial, I);
+    bind(ws->careful_items, I);
+    bind(ws->near_list, (size_t)near_cap);
+    bind(ws->fix_acc, P);
+    bind(ws->fp64_count, P);
+    bind(ws->flags, P);
+    bind(ws->counters, 8);
+    bind(ws->lk, P);
+    bind(ws->raw, P);
+    bind(ws->status, P);
+    return off;
+}
+
+}  // namespace
+
+struct lk_server {
+    lk_server_options opt;
+    int device = 0;
+    int num_sms = 1;
+    cudaStream_t stream = nullptr;
+    unsigned char* d_arena = nullptr;
+    unsigned char* h_arena = nullptr;
+    Arena dev, host;
+    std::deque<Request*> queue;
+    std::vector<Request*> running;     // admitted, in admission order
+    std::map<int64_t, Request*> all;
+    std::deque<Wave> waves;
+    bool slot_busy[kWaveSlots] = {};
+    lk::WaveSeg* h_segs[kWaveSlots] = {};   // pinned staging of each slot's runs
+    lk::WaveSeg* d_segs[kWaveSlots] = {};
+    unsigned long long* d_counters = nullptr;  // 2 per slot
+    int64_t next_ticket = 1;
+    lk_server_stats st{};
+    std::string err;
+};
+
+namespace {
+
+lk_status srv_fail(lk_server* s, lk_status st, const std::string& m) {
+    if (s) s->err = m;
+    set_global_error(m);
+    return st;
+}
+
+#define LK_SRV_CUDA(srv, call)                                                              \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return srv_fail(srv, e_ == cudaErrorMemoryAllocation ? LK_ERR_OOM : LK_ERR_CUDA, \
+                            std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    } while (0)
+
+lk::SweepArgs request_args(lk_ctx* ctx, Workspace& ws, const Packed& pk, int near_cap) {
+    lk::SweepArgs a{};
+    a.tasks = ws.tasks.p;
+    a.item_begin = ws.item_begin.p;
+    a.item_task = ws.item_task.p;
+    a.n_items = pk.n_items;
+    a.n_tasks = (int64_t)pk.tasks.size();
+    a.partial = ws.partial.p;
+    a.item_counter = ws.counters.p + 4;
+    a.overflow = ws.counters.p + 1;
+    unsigned int* u32 = reinterpret_cast<unsigned int*>(ws.counters.p + 2);
+    a.careful_count = u32 + 0;
+    a.careful_counter = u32 + 1;
+    a.near_count = u32 + 2;
+    a.careful_items = ws.careful_items.p;
+    a.near_list = ws.near_list.p;
+    a.near_capacity = near_cap;
+    a.fix_acc = ws.fix_acc.p;
+    a.fp64_count = ws.fp64_count.p;
+    a.flags = ws.flags.p;
+    a.near_ratio_sq = (float)(ctx->opt.near_ratio * ctx->opt.near_ratio);
+    return a;
+}
+
+// Retire finished waves (block on the oldest when `block`).
+lk_status retire(lk_server* s, bool block) {
+    while (!s->waves.empty()) {
+        Wave& w = s->waves.front();
+        cudaError_t e = block ? cudaEventSynchronize(w.done) : cudaEventQuery(w.done);
+        if (e == cudaErrorNotReady) break;
+        if (e != cudaSuccess) return srv_fail(s, LK_ERR_CUDA, std::string("lk_server_step: ") + cudaGetErrorString(e));
+        block = false;
+        for (Request* r : w.completing) {
+            r->state = kDone;
+            s->dev.release(r->dev_off, r->dev_bytes);
+            auto it = std::find(s->running.begin(), s->running.end(), r);
+            if (it != s->running.end()) s->running.erase(it);
+            s->st.completed += 1;
+        }
+        cudaEventDestroy(w.done);
+        s->slot_busy[w.slot] = false;
+        s->waves.pop_front();
+    }
+    return LK_OK;
+}
+
+// Admit queued requests in arrival order while slots and arena space last.
+lk_status admit(lk_server* s) {
+    while (!s->queue.empty() && (int)s->running.size() < s->opt.max_requests) {
+        Request* r = s->queue.front();
+        lk_ctx* ctx = r->ctx;
+        if (!r->packed) {
+            lk_status st = pack_pairs(ctx, r->pairs.data(), (int64_t)(r->pairs.size() / 2), r->pk);
+            if (st != LK_OK) return srv_fail(s, st, ctx->err);
+            r->packed = true;
+            Workspace probe;
+            r->dev_bytes = request_layout(r->pk, s->opt.near_capacity, &probe, 0);
+            r->host_bytes = r->pk.tasks.size() * 16 + 1024;
+        }
+        if (!s->dev.alloc(r->dev_bytes, &r->dev_off)) break;           // memory-based admission
+        if (!s->host.alloc(r->host_bytes, &r->host_off)) {
+            s->dev.release(r->dev_off, r->dev_bytes);
+            break;
+        }
+        request_layout(r->pk, s->opt.near_capacity, &r->ws, (uintptr_t)(s->d_arena + r->dev_off));
+        const size_t P = r->pk.tasks.size();
+        unsigned char* hb = s->h_arena + r->host_off;
+        r->h_lk = reinterpret_cast<int32_t*>(hb);
+        r->h_raw = reinterpret_cast<double*>(hb + ((P * 4 + 255) & ~(size_t)255));
+        r->h_status = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(r->h_raw) + ((P * 8 + 255) & ~(size_t)255));
+        r->args = request_args(ctx, r->ws, r->pk, s->opt.near_capacity);
+        lk_status st = upload_packed(ctx, r->ws, r->pk, s->stream);
+        if (st != LK_OK) return srv_fail(s, st, ctx->err);
+        const int64_t n = (int64_t)P;
+        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.counters.p, 0, 8 * sizeof(unsigned long long), s->stream));
+        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.fix_acc.p, 0, n * sizeof(unsigned long long), s->stream));
+        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.fp64_count.p, 0, n * sizeof(unsigned long long), s->stream));
+        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.flags.p, 0, n * sizeof(int), s->stream));
+        lk::launch_pair_frames(r->ws.tasks.p, n, ctx->d_aabb, s->stream);
+        r->state = kRunning;
+        r->next_item = 0;
+        s->running.push_back(r);
+        s->queue.pop_front();
+        s->st.admitted += 1;
+    }
+    return LK_OK;
+}
+
+// Launch one wave over the admitted requests' next items.
+lk_status launch_wave(lk_server* s) {
+    int slot = -1;
+    for (int k = 0; k < kWaveSlots; ++k)
+        if (!s->slot_busy[k]) { slot = k; break; }
+    if (slot < 0) return LK_OK;
+    bool any = false;
+    for (Request* r : s->running)
+        if (r->state == kRunning) { any = true; break; }
+    if (!any) return LK_OK;
+
+    lk::WaveSeg* segs = s->h_segs[slot];
+    int n_acc = 0, n_fast = 0;   // runs stored as [acc runs..., then fast runs from the end]
+    int64_t acc_items = 0, fast_items = 0;
+    int64_t budget = s->opt.wave_items;
+    std::vector<Request*> completing;
+    int64_t touched = 0;
+    for (Request* r : s->running) {
+        if (r->state != kRunning || budget <= 0 || n_acc + n_fast + 2 > kMaxSegs) continue;
+        ++touched;
+        const int64_t lo = r->next_item, hi = std::min<int64_t>(r->pk.n_items, lo + budget);
+        // accurate items are [0, n_acc_items), fast items after them
+        const int64_t a_lo = lo, a_hi = std::min(hi, r->pk.n_acc_items);
+        const int64_t f_lo = std::max(lo, r->pk.n_acc_items), f_hi = hi;
+        if (a_hi > a_lo) {
+            segs[n_acc] = lk::WaveSeg{r->args, a_lo, acc_items};
+            acc_items += a_hi - a_lo;
+            ++n_acc;
+        }
+        if (f_hi > f_lo) {
+            segs[kMaxSegs - 1 - n_fast] = lk::WaveSeg{r->args, f_lo, fast_items};
+            fast_items += f_hi - f_lo;
+            ++n_fast;
+        }
+        budget -= hi - lo;
+        r->next_item = hi;
+        if (hi >= r->pk.n_items) {
+            r->state = kLaunched;
+            completing.push_back(r);
+        }
+    }
+    // fast runs were written backwards from the end; put them after the accurate ones
+    std::reverse(segs + kMaxSegs - n_fast, segs + kMaxSegs);
+    std::copy(segs + kMaxSegs - n_fast, segs + kMaxSegs, segs + n_acc);
+    cudaStream_t st = s->stream;
+    LK_SRV_CUDA(s, cudaMemcpyAsync(s->d_segs[slot], segs, (size_t)(n_acc + n_fast) * sizeof(lk::WaveSeg),
+                                   cudaMemcpyHostToDevice, st));
+    unsigned long long* cnt = s->d_counters + 2 * slot;
+    LK_SRV_CUDA(s, cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
+    lk::launch_wave(s->d_segs[slot], n_acc, acc_items, true, cnt, s->num_sms * lk::wave_blocks_per_sm(true), st);
+    lk::launch_wave(s->d_segs[slot] + n_acc, n_fast, fast_items, false, cnt + 1,
+                    s->num_sms * lk::wave_blocks_per_sm(false), st);
+    for (Request* r : completing) {
+        lk::launch_sweep_careful(r->args, s->num_sms, st);
+        lk::launch_near_fix(r->args, s->num_sms * 4, st);
+        lk::ReduceArgs ra{};
+        ra.tasks = r->ws.tasks.p;
+        ra.item_begin = r->ws.item_begin.p;
+        ra.partial = r->ws.partial.p;
+        ra.fix_acc = r->ws.fix_acc.p;
+        ra.flags = r->ws.flags.p;
+        ra.n_tasks = (int64_t)r->pk.tasks.size();
+        ra.int_tol = r->ctx->opt.int_tol;
+        ra.lk_out = r->ws.lk.p;
+        ra.raw_out = r->ws.raw.p;
+        ra.status_out = r->ws.status.p;
+        lk::launch_reduce(ra, st);
+        const size_t P = r->pk.tasks.size();
+        LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_lk, r->ws.lk.p, P * 4, cudaMemcpyDeviceToHost, st));
+        LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_raw, r->ws.raw.p, P * 8, cudaMemcpyDeviceToHost, st));
+        LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_status, r->ws.status.p, P * 4, cudaMemcpyDeviceToHost, st));
+    }
+    LK_SRV_CUDA(s, cudaGetLastError());
+    Wave w;
+    w.slot = slot;
+    w.completing = completing;
+    LK_SRV_CUDA(s, cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming));
+    LK_SRV_CUDA(s, cudaEventRecord(w.done, st));
+    s->slot_busy[slot] = true;
+    s->waves.push_back(w);
+    s->st.waves += 1;
+    s->st.max_requests_per_wave = std::max<int64_t>(s->st.max_requests_per_wave, touched);
+    s->st.items_launched += acc_items + fast_items;
+    return LK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lk_server_default_options(lk_server_options* o) {
+    if (!o) return;
+    o->max_requests = 64;
+    o->arena_bytes = (size_t)1 << 30;
+    o->host_bytes = (size_t)64 << 20;
+    o->wave_items = 16384;
+    o->near_capacity = 4096;
+    o->max_queue = 1 << 16;
+}
+
+lk_status lk_server_create(lk_server** out, const lk_server_options* opt) {
+    if (!out) return srv_fail(nullptr, LK_ERR_ARG, "lk_server_create: out is NULL");
+    *out = nullptr;
+    lk_server_options o;
+    lk_server_default_options(&o);
+    if (opt) o = *opt;
+    if (o.max_requests < 1 || o.wave_items < 1 || o.near_capacity < 1 || o.arena_bytes < 4096 ||
+        o.host_bytes < 4096 || o.max_queue < 1)
+        return srv_fail(nullptr, LK_ERR_ARG, "lk_server_create: invalid options");
+    lk_server* s = new lk_server();
+    s->opt = o;
+    cudaGetDevice(&s->device);
+    cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_arena, o.arena_bytes);
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_arena, o.host_bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_counters, 2 * kWaveSlots * sizeof(unsigned long long));
+    for (int k = 0; k < kWaveSlots && e == cudaSuccess; ++k) {
+        e = cudaHostAlloc(&s->h_segs[k], kMaxSegs * sizeof(lk::WaveSeg), cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_segs[k], kMaxSegs * sizeof(lk::WaveSeg));
+    }
+    if (e != cudaSuccess) {
+        lk_server_destroy(s);
+        return srv_fail(nullptr, e == cudaErrorMemoryAllocation ? LK_ERR_OOM : LK_ERR_CUDA,
+                        std::string("lk_server_create: ") + cudaGetErrorString(e));
+    }
+    s->dev.init(o.arena_bytes);
+    s->host.init(o.host_bytes);
+    *out = s;
+    return LK_OK;
+}
+
+void* lk_server_stream(lk_server* s) { return s ? (void*)s->stream : nullptr; }
+
+lk_status lk_server_submit(lk_server* s, lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs,
+                           int64_t* ticket) {
+    if (!s) return srv_fail(nullptr, LK_ERR_ARG, "lk_server_submit: NULL server");
+    if (!ctx || !ticket || n_pairs < 1 || n_pairs > INT32_MAX || !loop_pairs)
+        return srv_fail(s, LK_ERR_ARG, "lk_server_submit: invalid arguments");
+    if (ctx->opt.precision != LK_MIXED)
+        return srv_fail(s, LK_ERR_ARG, "lk_server_submit: the server runs the mixed-precision path");
+    if ((int64_t)s->queue.size() >= s->opt.max_queue)
+        return srv_fail(s, LK_ERR_BUSY, "lk_server_submit: queue full");
+    Request* r = new Request();
+    r->ctx = ctx;
+    r->pairs.resize((size_t)(2 * n_pairs));
+    if (is_device_ptr(loop_pairs)) {
+        if (cudaMemcpy(r->pairs.data(), loop_pairs, 2 * n_pairs * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            delete r;
+            return srv_fail(s, LK_ERR_CUDA, "lk_server_submit: cannot read loop_pairs");
+        }
+    } else {
+        std::memcpy(r->pairs.data(), loop_pairs, 2 * n_pairs * sizeof(int32_t));
+    }
+    // A request that could never fit is refused now rather than blocking the queue.
+    lk_status st = pack_pairs(ctx, r->pairs.data(), n_pairs, r->pk);
+    if (st != LK_OK) {
+        delete r;
+        return srv_fail(s, st, ctx->err);
+    }
+    r->packed = true;
+    Workspace probe;
+    r->dev_bytes = request_layout(r->pk, s->opt.near_capacity, &probe, 0);
+    r->host_bytes = r->pk.tasks.size() * 16 + 1024;
+    if (Arena::round(r->dev_bytes) > s->opt.arena_bytes || Arena::round(r->host_bytes) > s->opt.host_bytes) {
+        delete r;
+        return srv_fail(s, LK_ERR_OOM, "lk_server_submit: request larger than the server's arena");
+    }
+    r->ticket = s->next_ticket++;
+    s->queue.push_back(r);
+    s->all[r->ticket] = r;
+    s->st.submitted += 1;
+    *ticket = r->ticket;
+    return LK_OK;
+}
+
+lk_status lk_server_step(lk_server* s, int wait) {
+    if (!s) return srv_fail(nullptr, LK_ERR_ARG, "lk_server_step: NULL server");
+    lk_status st = retire(s, false);
+    if (st != LK_OK) return st;
+    if ((st = admit(s)) != LK_OK) return st;
+    if ((st = launch_wave(s)) != LK_OK) return st;
+    if (wait && !s->waves.empty() && (st = retire(s, true)) != LK_OK) return st;
+    return LK_OK;
+}
+
+lk_status lk_server_poll(lk_server* s, int64_t ticket, int* done, int32_t* lk_out, double* raw_out,
+                         int32_t* status_out) {
+    if (!s || !done) return srv_fail(s, LK_ERR_ARG, "lk_server_poll: NULL argument");
+    *done = 0;
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return srv_fail(s, LK_ERR_ARG, "lk_server_poll: unknown ticket");
+    Request* r = it->second;
+    if (r->state != kDone) return LK_OK;
+    const size_t P = r->pk.tasks.size();
+    // The pinned buffers are indexed by the caller's pair order already (the
+    // reduction writes through out_index).
+    if (lk_out) std::memcpy(lk_out, r->h_lk, P * 4);
+    if (raw_out) std::memcpy(raw_out, r->h_raw, P * 8);
+    if (status_out) std::memcpy(status_out, r->h_status, P * 4);
+    s->host.release(r->host_off, r->host_bytes);
+    s->all.erase(it);
+    delete r;
+    *done = 1;
+    return LK_OK;
+}
+
+lk_status lk_server_get_stats(lk_server* s, lk_server_stats* out) {
+    if (!s || !out) return srv_fail(s, LK_ERR_ARG, "lk_server_get_stats: NULL argument");
+    s->st.queued = (int64_t)s->queue.size();
+    s->st.running = (int64_t)s->running.size();
+    s->st.arena_used = (int64_t)s->dev.used;
+    s->st.waves_in_flight = (int64_t)s->waves.size();
+    *out = s->st;
+    return LK_OK;
+}
+
+const char* lk_server_last_error(const lk_server* s) {
+    if (s) return s->err.c_str();
+    return lk_last_error(nullptr);
+}
+
+void lk_server_destroy(lk_server* s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (Wave& w : s->waves) cudaEventDestroy(w.done);
+    for (auto& kv : s->all) delete kv.second;
+    for (int k = 0; k < kWaveSlots; ++k) {
+        if (s->h_segs[k]) cudaFreeHost(s->h_segs[k]);
+        if (s->d_segs[k]) cudaFree(s->d_segs[k]);
+    }
+    if (s->d_counters) cudaFree(s->d_counters);
+    if (s->d_arena) cudaFree(s->d_arena);
+    if (s->h_arena) cudaFreeHost(s->h_arena);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+}  // extern "C"

@@ -18,7 +18,7 @@ struct __align__(32) Vtx {
 constexpr int kLaneCols = 4;
 constexpr int kTileCols = 32 * kLaneCols;
 constexpr int kChunkRows = 32;
-constexpr int kSweepWarps = 8;
+constexpr int kSweepWarps = 4;
 constexpr int kSweepThreads = 32 * kSweepWarps;
 
 // All-FP64 baseline sweep: one column per lane.
@@ -34,6 +34,7 @@ constexpr int kFlagIntersect = 1;
 
 // One loop pair of a verify call, laid out for the device.
 struct PairTask {
+    const Vtx* V;        // the geometry this pair's loops live in
     int64_t row_base;    // first vertex of the row loop (segments j, iterated)
     int64_t col_base;    // first vertex of the column loop (segments i, across lanes)
     int32_t n_rows;      // segments (= vertices) of the row loop
@@ -59,7 +60,6 @@ struct NearEntry {
 };
 
 struct SweepArgs {
-    const Vtx* V;                  // resident vertices, FP64
     const PairTask* tasks;
     const int64_t* item_begin;     // [n_tasks+1] first item of each task
     const int32_t* item_task;      // [n_items] task of each item
@@ -78,6 +78,13 @@ struct SweepArgs {
     unsigned long long* overflow;  // [1] recomputes evaluated in place (list full)
     int* flags;                    // [n_tasks] kFlag* bits
     float near_ratio_sq;           // tau^2
+};
+
+// One request's contiguous run of items inside a serving wave.
+struct WaveSeg {
+    SweepArgs args;        // the request's arrays
+    int64_t item_lo;       // first request-local item of the run
+    int64_t wave_base;     // wave-global index of that item
 };
 
 struct ReduceArgs {
@@ -102,6 +109,9 @@ void launch_sweep_mixed(const SweepArgs& a, bool accurate, int64_t item_lo, int6
 void launch_sweep_f64(const SweepArgs& a, int grid, cudaStream_t s);
 void launch_sweep_careful(const SweepArgs& a, int grid, cudaStream_t s);
 void launch_near_fix(const SweepArgs& a, int grid, cudaStream_t s);
+void launch_wave(const WaveSeg* segs, int n_segs, int64_t n_items, bool accurate,
+                 unsigned long long* counter, int grid, cudaStream_t s);
+int wave_blocks_per_sm(bool accurate);
 void launch_reduce(const ReduceArgs& a, cudaStream_t s);
 void launch_update(Vtx* V, const void* data, int dtype, int is_delta, int64_t n, cudaStream_t s);
 int sweep_mixed_blocks_per_sm(bool accurate);

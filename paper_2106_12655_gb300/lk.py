@@ -35,7 +35,9 @@ STATUS_NAMES = {0: "LK_OK", 1: "LK_ERR_ARG", 2: "LK_ERR_ZERO_SEGMENT", 3: "LK_ER
 
 EXPORTED = ["lk_default_options", "lk_create", "lk_update", "lk_verify", "lk_sync", "lk_get_stats",
             "lk_destroy", "lk_last_error", "lk_plan_create", "lk_plan_run", "lk_plan_destroy",
-            "lk_verify_noalloc"]
+            "lk_verify_noalloc", "lk_server_default_options", "lk_server_create", "lk_server_stream",
+            "lk_server_submit", "lk_server_step", "lk_server_poll", "lk_server_get_stats",
+            "lk_server_last_error", "lk_server_destroy"]
 
 
 class lk_options(ctypes.Structure):
@@ -51,6 +53,18 @@ class lk_stats(ctypes.Structure):
                 ("near_overflow", ctypes.c_int64), ("tile_rows", ctypes.c_int32),
                 ("tile_cols", ctypes.c_int32), ("careful_items", ctypes.c_int64),
                 ("sweep_ms", ctypes.c_double)]
+
+
+class lk_server_options(ctypes.Structure):
+    _fields_ = [("max_requests", ctypes.c_int), ("arena_bytes", ctypes.c_size_t),
+                ("host_bytes", ctypes.c_size_t), ("wave_items", ctypes.c_int64),
+                ("near_capacity", ctypes.c_int), ("max_queue", ctypes.c_int)]
+
+
+class lk_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "queued", "running",
+                                               "waves", "waves_in_flight", "items_launched",
+                                               "max_requests_per_wave", "arena_used")]
 
 
 class LkError(RuntimeError):
@@ -99,6 +113,24 @@ def load(path: str | None = None):
     lib.lk_plan_run.argtypes = [vp, vp, vp, vp, vp]
     lib.lk_plan_destroy.restype = None
     lib.lk_plan_destroy.argtypes = [vp]
+    lib.lk_server_default_options.restype = None
+    lib.lk_server_default_options.argtypes = [ctypes.POINTER(lk_server_options)]
+    lib.lk_server_create.restype = ctypes.c_int
+    lib.lk_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(lk_server_options)]
+    lib.lk_server_stream.restype = vp
+    lib.lk_server_stream.argtypes = [vp]
+    lib.lk_server_submit.restype = ctypes.c_int
+    lib.lk_server_submit.argtypes = [vp, vp, i32p, i64, ctypes.POINTER(ctypes.c_int64)]
+    lib.lk_server_step.restype = ctypes.c_int
+    lib.lk_server_step.argtypes = [vp, ctypes.c_int]
+    lib.lk_server_poll.restype = ctypes.c_int
+    lib.lk_server_poll.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int), vp, vp, vp]
+    lib.lk_server_get_stats.restype = ctypes.c_int
+    lib.lk_server_get_stats.argtypes = [vp, ctypes.POINTER(lk_server_stats)]
+    lib.lk_server_last_error.restype = ctypes.c_char_p
+    lib.lk_server_last_error.argtypes = [vp]
+    lib.lk_server_destroy.restype = None
+    lib.lk_server_destroy.argtypes = [vp]
     lib.lk_verify_noalloc.restype = ctypes.c_int
     lib.lk_verify_noalloc.argtypes = [vp, ctypes.c_int, i64, vp, i64, i32p, i64, vp, vp, vp, vp]
     _lib = lib
@@ -234,6 +266,64 @@ def lk_verify_noalloc(vertices, loop_offsets, loop_pairs, lk_out=None, raw_out=N
                                     _ptr(loop_offsets), int(loop_offsets.shape[0]) - 1, _ptr(loop_pairs),
                                     int(loop_pairs.shape[0]), _ptr(lk_out), _ptr(raw_out), _ptr(status_out),
                                     _stream(stream)))
+
+
+def _check_srv(status, srv):
+    if status != LK_OK:
+        msg = load().lk_server_last_error(srv)
+        raise LkError(status, msg.decode() if msg else "")
+
+
+def lk_server_default_options() -> lk_server_options:
+    o = lk_server_options()
+    load().lk_server_default_options(ctypes.byref(o))
+    return o
+
+
+def lk_server_create(options: lk_server_options | None = None):
+    out = ctypes.c_void_p()
+    _check_srv(load().lk_server_create(ctypes.byref(out), ctypes.byref(options) if options is not None else None),
+               None)
+    return out.value
+
+
+def lk_server_stream(srv) -> int:
+    return load().lk_server_stream(srv) or 0
+
+
+def lk_server_submit(srv, ctx, loop_pairs) -> int:
+    if str(loop_pairs.dtype).split(".")[-1] != "int32":
+        raise TypeError("loop_pairs must be int32")
+    t = ctypes.c_int64()
+    _check_srv(load().lk_server_submit(srv, ctx, _ptr(loop_pairs), int(loop_pairs.shape[0]), ctypes.byref(t)), srv)
+    return t.value
+
+
+def lk_server_step(srv, wait: bool = False):
+    _check_srv(load().lk_server_step(srv, 1 if wait else 0), srv)
+
+
+def lk_server_poll(srv, ticket, lk_out=None, raw_out=None, status_out=None) -> bool:
+    d = ctypes.c_int()
+    _check_srv(load().lk_server_poll(srv, ticket, ctypes.byref(d), _ptr(lk_out), _ptr(raw_out), _ptr(status_out)),
+               srv)
+    return bool(d.value)
+
+
+def lk_server_get_stats(srv) -> dict:
+    s = lk_server_stats()
+    _check_srv(load().lk_server_get_stats(srv, ctypes.byref(s)), srv)
+    return {k: getattr(s, k) for k, _ in lk_server_stats._fields_}
+
+
+def lk_server_last_error(srv=None) -> str:
+    m = load().lk_server_last_error(srv)
+    return m.decode() if m else ""
+
+
+def lk_server_destroy(srv):
+    if srv:
+        load().lk_server_destroy(srv)
 
 
 # ----------------------------------------------------------------------------- convenience

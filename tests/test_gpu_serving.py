@@ -1,0 +1,150 @@
+"""Serving (continuous batching): results alone and in the mix, admission by
+memory, geometry kept resident and updated between requests."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2106_12655_gb300 import lk
+from paper_2106_12655_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_12655_gb300 import build as B
+
+    B.build()
+    lk.load()
+
+
+def alone(ctx, pairs):
+    n = pairs.shape[0]
+    out = np.zeros(n, np.int32), np.zeros(n), np.zeros(n, np.int32)
+    lk.lk_verify(ctx, pairs, *out)
+    return out
+
+
+def drain(srv, tickets, sizes, max_steps=100000):
+    res = {}
+    for _ in range(max_steps):
+        lk.lk_server_step(srv, wait=True)
+        for t in list(tickets):
+            if t in res:
+                continue
+            n = sizes[t]
+            out = np.zeros(n, np.int32), np.zeros(n), np.zeros(n, np.int32)
+            if lk.lk_server_poll(srv, t, *out):
+                res[t] = out
+        if len(res) == len(tickets):
+            return res
+    raise AssertionError("server did not finish")
+
+
+def scenes():
+    # several resident geometries: small piles of various ring and segment counts
+    gs = [W.chainmail(seed=40 + k, rows=6 + 2 * k, cols=8 + 3 * k, nseg=None,
+                      nseg_per_ring=np.random.default_rng(k).integers(64, 257, size=(6 + 2 * k) * (8 + 3 * k)))
+          for k in range(4)]
+    gs.append(W.torus_link(2, 3, 3000, dtype=np.float32, n2=2900))     # an accurate-variant request
+    return gs
+
+
+def test_results_alone_and_in_the_mix_are_identical():
+    gs = scenes()
+    ctxs = [lk.lk_create(g.vertices, g.offsets) for g in gs]
+    o = lk.lk_server_default_options()
+    o.wave_items = 512                       # small waves: requests span several, and share them
+    srv = lk.lk_server_create(o)
+    try:
+        refs, tickets, sizes, which = {}, [], {}, {}
+        rng = np.random.default_rng(0)
+        for rep in range(3):
+            for k, (g, ctx) in enumerate(zip(gs, ctxs)):
+                pairs = g.pairs if rep == 0 else g.pairs[rng.permutation(g.pairs.shape[0])][: max(1, g.pairs.shape[0] // 2)]
+                pairs = np.ascontiguousarray(pairs)
+                t = lk.lk_server_submit(srv, ctx, pairs)
+                tickets.append(t)
+                sizes[t] = pairs.shape[0]
+                which[t] = (k, pairs)
+                if rep == 1:
+                    lk.lk_server_step(srv)           # let some run while the rest arrive
+        res = drain(srv, tickets, sizes)
+        st = lk.lk_server_get_stats(srv)
+        assert st["completed"] == len(tickets)
+        assert st["max_requests_per_wave"] >= 2          # work of several requests overlapped
+        for t in tickets:
+            k, pairs = which[t]
+            ref = alone(ctxs[k], pairs)
+            got = res[t]
+            assert np.array_equal(got[2], ref[2])
+            assert np.array_equal(got[0], ref[0])
+            assert np.max(np.abs(got[1] - ref[1])) <= 1e-12
+        # and against the oracle for one request of each scene
+        for k, g in enumerate(gs):
+            t = next(t for t in tickets if which[t][0] == k)
+            ref = O.link_pairs(g.vertices, g.offsets, which[t][1])
+            assert np.max(np.abs(res[t][1] - ref)) <= 1e-6
+            assert np.array_equal(res[t][0], O.round_lk(ref).astype(np.int32))
+    finally:
+        lk.lk_server_destroy(srv)
+        for c in ctxs:
+            lk.lk_destroy(c)
+
+
+def test_admission_waits_for_arena_memory():
+    g = W.chainmail(seed=7, rows=8, cols=16)
+    ctx = lk.lk_create(g.vertices, g.offsets)
+    o = lk.lk_server_default_options()
+    o.arena_bytes = 300 << 10                # room for one request of this size at a time
+    o.wave_items = 256
+    srv = lk.lk_server_create(o)
+    try:
+        tickets, sizes = [], {}
+        for _ in range(4):
+            t = lk.lk_server_submit(srv, ctx, g.pairs)
+            tickets.append(t)
+            sizes[t] = g.pairs.shape[0]
+        lk.lk_server_step(srv)
+        st = lk.lk_server_get_stats(srv)
+        assert st["running"] == 1 and st["queued"] == 3       # admission held back by memory
+        assert st["arena_used"] <= o.arena_bytes
+        res = drain(srv, tickets, sizes)
+        ref = alone(ctx, g.pairs)
+        for t in tickets:
+            assert np.array_equal(res[t][1], ref[1])
+        too_big = W.chainmail(seed=8, rows=32, cols=64)
+        ctx2 = lk.lk_create(too_big.vertices, too_big.offsets)
+        with pytest.raises(lk.LkError) as ei:
+            lk.lk_server_submit(srv, ctx2, too_big.pairs)
+        assert ei.value.status == lk.LK_ERR_OOM
+        lk.lk_destroy(ctx2)
+    finally:
+        lk.lk_server_destroy(srv)
+        lk.lk_destroy(ctx)
+
+
+def test_resident_geometry_updated_between_requests():
+    g = W.chainmail(seed=11, rows=6, cols=10)
+    ctx = lk.lk_create(g.vertices, g.offsets)
+    srv = lk.lk_server_create(None)
+    stream = lk.lk_server_stream(srv)
+    rng = np.random.default_rng(2)
+    verts = g.vertices.astype(np.float64).copy()
+    try:
+        for step in range(3):
+            delta = rng.normal(scale=2e-3, size=g.vertices.shape).astype(np.float32)
+            lk.lk_update(ctx, delta, True, stream)   # ordered before the request on the server's stream
+            verts += delta.astype(np.float64)
+            t = lk.lk_server_submit(srv, ctx, g.pairs)
+            res = drain(srv, [t], {t: g.pairs.shape[0]})[t]
+            ref = O.link_pairs(verts, g.offsets, g.pairs)
+            assert np.all(res[2] == 0)
+            assert np.array_equal(res[0], O.round_lk(ref).astype(np.int32))
+            assert np.max(np.abs(res[1] - ref)) <= 1e-6
+    finally:
+        lk.lk_server_destroy(srv)
+        lk.lk_destroy(ctx)
