@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=600)
     return ap.parse_args()
 
 
@@ -118,6 +120,43 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def serving_block(args):
+    """Open-loop Poisson serving over resident chainmail piles (500-14,000 rings,
+    64-256 segments per ring, 1k-20k pairs per request): capacity, then p50/p99
+    latency at 50/80/95% of it."""
+    from paper_2106_12655_gb300 import lk
+    from paper_2106_12655_gb300 import serving as S
+
+    scenes = S.make_scenes(seed=5, n_scenes=6)
+    srv = lk.lk_server_create(None)
+    try:
+        warm = S.request_plan(scenes, 40, seed=99)
+        S.run(srv, scenes, warm, None)
+        cap_plan = S.request_plan(scenes, max(100, args.serving_requests // 2), seed=1)
+        lat, wall, bad = S.run(srv, scenes, cap_plan, None)
+        pairs, sps = S.plan_sizes(scenes, cap_plan)
+        cap = len(cap_plan) / wall
+        out = {"scenes": [{"rings": sc.geometry.n_loops, "vertices": int(sc.geometry.vertices.shape[0]),
+                           "pairs": int(sc.geometry.pairs.shape[0])} for sc in scenes],
+               "capacity": {"req_per_s": cap, "pairs_per_s": pairs.sum() / wall, "sp_per_s": sps.sum() / wall,
+                            "n_requests": len(cap_plan), "nonok_pair_status": bad},
+               "loads": []}
+        for load in (0.5, 0.8, 0.95):
+            plan = S.request_plan(scenes, args.serving_requests, seed=int(load * 100))
+            lat, wall, bad = S.run(srv, scenes, plan, rate_per_s=load * cap, seed=int(load * 1000))
+            pairs, sps = S.plan_sizes(scenes, plan)
+            out["loads"].append({"load": load, "offered_req_per_s": load * cap, "req_per_s": len(plan) / wall,
+                                 "pairs_per_s": pairs.sum() / wall, "sp_per_s": sps.sum() / wall,
+                                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                                 "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                                 "n_requests": len(plan), "nonok_pair_status": bad})
+        out["server_stats"] = lk.lk_server_get_stats(srv)
+        return out
+    finally:
+        lk.lk_server_destroy(srv)
+        S.close(scenes)
 
 
 def cpu_baseline(g):
@@ -307,7 +346,7 @@ def run_ours(args):
         "fp64_baseline": {"value": fp64_value, "unit": UNIT, "ms_per_step": statistics.median(f64_ms),
                           "speedup_mixed_over_fp64": value / world / fp64_value,
                           "max_abs_raw_diff_vs_mixed": float(np.max(np.abs(raw64_host - raw_host)))},
-        "fp64_recomputed_segment_pairs": stats["fp64_pairs"], "careful_items": stats["careful_items"],
+        "fp64_recomputed_segment_pairs": stats["fp64_pairs"], "careful_items": stats["careful_items"], "careful_chunks": stats["careful_chunks"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "sweep_mixed_kernel",
                      "kernel_ms": sweep_avg, "flops_per_segment_pair": FLOPS_PER_SP,
@@ -317,6 +356,8 @@ def run_ours(args):
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clk, "wall_s_timed_region": wall,
     }
+    if not args.no_serving and world == 1:
+        line["serving"] = serving_block(args)
     if not args.no_cpu_baseline and world == 1:
         ref_raw, cb = cpu_baseline(g)
         line["cpu_baseline"] = cb

@@ -64,8 +64,9 @@ typedef enum {
 
 typedef struct lk_options {
     int precision;       /* lk_precision, default LK_MIXED */
-    double near_ratio;   /* tau >= 4: a segment pair (j,i) with |l_j - k_i| < tau*max(|s_j|,|s_i|)
-                            is evaluated in FP64 (default 4.0) */
+    double near_ratio;   /* tau >= 3: a segment pair whose nearest corner distance (the smallest
+                            of |l_j-k_i|, |l_j-k_{i+1}|, |l_{j+1}-k_i|, |l_{j+1}-k_{i+1}|) is below
+                            tau*max(|s_j|,|s_i|) is evaluated in FP64 (default 3.0) */
     double int_tol;      /* per-pair status LK_ERR_NONINTEGER when |raw - lk| > int_tol (default 0.1) */
     size_t mem_budget;   /* device bytes one verify may use for its work buffers, 0 = unlimited */
     int tile_rows;       /* rows per work item; 0 = chosen by the built-in tuner */
@@ -73,6 +74,8 @@ typedef struct lk_options {
                             evaluated in place, results are unchanged */
     int timing;          /* 1: time the bulk sweep kernel with CUDA events on the launch stream
                             (read back by lk_get_stats as sweep_ms); default 0 */
+    int chunk_capacity;  /* entries of the chunk hand-over list (default 1<<20); an overflow
+                            hands whole items to the careful pass instead, results unchanged */
     int64_t accurate_threshold; /* LK_MIXED: loop pairs with at least this many segment pairs use
                             the bias-free FP32 arithmetic (refined sqrt and division, shifted
                             denominators); smaller pairs use the hardware approximations,
@@ -88,8 +91,9 @@ typedef struct lk_stats {
     int64_t near_overflow;    /* FP64 recomputes that did not fit the list */
     int32_t tile_rows;        /* rows per work item used */
     int32_t tile_cols;        /* columns per work item used */
-    int64_t careful_items;    /* items swept again with per-pair tests */
+    int64_t careful_items;    /* whole items swept again with per-pair tests (chunk list full) */
     double sweep_ms;          /* bulk sweep kernel time (options.timing = 1), else -1 */
+    int64_t careful_chunks;   /* 32-row chunks swept again with per-pair tests */
 } lk_stats;
 
 typedef struct lk_ctx lk_ctx;
@@ -195,7 +199,7 @@ void lk_plan_destroy(lk_plan* plan);
 typedef struct lk_server_options {
     int max_requests;     /* requests admitted at once (default 64) */
     size_t arena_bytes;   /* device memory for request work buffers (default 1 GiB) */
-    size_t host_bytes;    /* pinned host memory for results (default 64 MiB) */
+    size_t host_bytes;    /* pinned host memory for staged item tables and results (default 256 MiB) */
     int64_t wave_items;   /* work items per wave (default 16384) */
     int near_capacity;    /* FP64 recompute list entries per request (default 4096) */
     int max_queue;        /* queued requests before submit returns LK_ERR_BUSY (default 65536) */

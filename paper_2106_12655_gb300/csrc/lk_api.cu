@@ -79,6 +79,7 @@ struct Packed {
     std::vector<int32_t> item_task;
     int64_t n_items = 0;
     int64_t n_acc_items = 0;   // items [0, n_acc_items) belong to accurate-variant pairs
+    int64_t n_chunks = 0;      // 32-row chunks over all items
     int64_t segment_pairs = 0;
     int tile_rows_max = 0;
     int tile_cols = 0;
@@ -91,6 +92,8 @@ struct Workspace {
     DevBuf<int32_t> item_task;
     DevBuf<double> partial;
     DevBuf<int64_t> careful_items;
+    DevBuf<lk::CarefulChunk> careful_chunks;
+    DevBuf<unsigned long long> item_fix;
     DevBuf<NearEntry> near_list;
     DevBuf<unsigned long long> fix_acc;
     DevBuf<unsigned long long> fp64_count;
@@ -115,7 +118,7 @@ struct Workspace {
         if (ev1) cudaEventDestroy(ev1);
         ev0 = ev1 = nullptr;
         tasks.release(); item_begin.release(); item_task.release(); partial.release();
-        careful_items.release(); near_list.release(); fix_acc.release(); fp64_count.release();
+        careful_items.release(); careful_chunks.release(); item_fix.release(); near_list.release(); fix_acc.release(); fp64_count.release();
         flags.release(); counters.release(); lk.release(); raw.release(); status.release();
     }
 };
@@ -248,6 +251,17 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
     pk.tasks.swap(sorted);
     pk.n_items = pk.item_begin[(size_t)n];
     pk.n_acc_items = 0;
+    pk.n_chunks = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        const PairTask& t = pk.tasks[(size_t)k];
+        if (t.status != LK_OK) continue;
+        const int64_t row_tiles = (t.n_rows + t.tile_rows - 1) / t.tile_rows;
+        const int64_t full = t.n_rows / t.tile_rows, last = t.n_rows - full * t.tile_rows;
+        const int64_t chunks_per_col = full * ((t.tile_rows + lk::kChunkRows - 1) / lk::kChunkRows) +
+                                       (last > 0 ? (last + lk::kChunkRows - 1) / lk::kChunkRows : 0);
+        (void)row_tiles;
+        pk.n_chunks += chunks_per_col * t.col_tiles;
+    }
     for (int64_t k = 0; k < n; ++k)
         if (pk.tasks[(size_t)k].accurate) pk.n_acc_items = pk.item_begin[(size_t)k + 1];
     if (pk.n_items > (int64_t)INT32_MAX * 16)
@@ -259,14 +273,24 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
     return LK_OK;
 }
 
-size_t workspace_bytes(const lk_ctx* ctx, int64_t n_tasks, int64_t n_items) {
+size_t chunk_capacity(const lk_options& o, int64_t n_chunks);
+
+size_t workspace_bytes(const lk_ctx* ctx, int64_t n_tasks, int64_t n_items, int64_t n_chunks) {
     const size_t near = (size_t)std::max(0, ctx->opt.near_capacity);
-    return n_tasks * (sizeof(PairTask) + 8 + 8 + 8 + 4 + 4 + 8 + 4) + n_items * (4 + 8 + 8) +
+    return n_tasks * (sizeof(PairTask) + 8 + 8 + 8 + 4 + 4 + 8 + 4) + n_items * (4 + 8 + 8 + 8) +
+           chunk_capacity(ctx->opt, n_chunks) * sizeof(lk::CarefulChunk) +
            near * sizeof(NearEntry) + 64;
 }
 
-lk_status ensure_workspace(lk_ctx* ctx, Workspace& ws, int64_t n_tasks, int64_t n_items) {
-    if (ctx->opt.mem_budget > 0 && workspace_bytes(ctx, n_tasks, n_items) > ctx->opt.mem_budget)
+// Entries of the chunk hand-over list: every chunk of the batch, at most the
+// configured capacity (an overflow hands whole items over instead).
+size_t chunk_capacity(const lk_options& o, int64_t n_chunks) {
+    const int64_t cap = o.chunk_capacity > 0 ? o.chunk_capacity : (int64_t)1 << 20;
+    return (size_t)std::max<int64_t>(1, std::min<int64_t>(n_chunks, cap));
+}
+
+lk_status ensure_workspace(lk_ctx* ctx, Workspace& ws, int64_t n_tasks, int64_t n_items, int64_t n_chunks) {
+    if (ctx->opt.mem_budget > 0 && workspace_bytes(ctx, n_tasks, n_items, n_chunks) > ctx->opt.mem_budget)
         return fail(ctx, LK_ERR_OOM, "lk_verify: work buffers exceed mem_budget");
     const size_t nt = (size_t)std::max<int64_t>(n_tasks, 1), ni = (size_t)std::max<int64_t>(n_items, 1);
     LK_CUDA(ctx, ws.tasks.ensure(nt));
@@ -274,6 +298,8 @@ lk_status ensure_workspace(lk_ctx* ctx, Workspace& ws, int64_t n_tasks, int64_t 
     LK_CUDA(ctx, ws.item_task.ensure(ni));
     LK_CUDA(ctx, ws.partial.ensure(ni));
     LK_CUDA(ctx, ws.careful_items.ensure(ni));
+    LK_CUDA(ctx, ws.careful_chunks.ensure(chunk_capacity(ctx->opt, n_chunks)));
+    LK_CUDA(ctx, ws.item_fix.ensure(ni));
     LK_CUDA(ctx, ws.near_list.ensure((size_t)std::max(1, ctx->opt.near_capacity)));
     LK_CUDA(ctx, ws.fix_acc.ensure(nt));
     LK_CUDA(ctx, ws.fp64_count.ensure(nt));
@@ -314,6 +340,11 @@ lk::SweepArgs sweep_args(const lk_ctx* ctx, Workspace& ws, const Packed& pk) {
     a.near_count = u32 + 2;   // low half of counters[3]
     a.n_tasks = (int64_t)pk.tasks.size();
     a.careful_items = ws.careful_items.p;
+    a.careful_chunks = ws.careful_chunks.p;
+    a.chunk_capacity = (int)std::min<size_t>(ws.careful_chunks.cap, (size_t)INT32_MAX);
+    a.chunk_count = u32 + 6;     // low half of counters[5]
+    a.chunk_counter = u32 + 7;   // high half of counters[5], low half of counters[6]
+    a.item_fix = ws.item_fix.p;
     a.near_list = ws.near_list.p;
     a.near_capacity = std::max(1, ctx->opt.near_capacity);
     a.fix_acc = ws.fix_acc.p;
@@ -341,6 +372,8 @@ lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStrea
     LK_CUDA(ctx, cudaMemsetAsync(ws.fix_acc.p, 0, n * sizeof(unsigned long long), s));
     LK_CUDA(ctx, cudaMemsetAsync(ws.fp64_count.p, 0, n * sizeof(unsigned long long), s));
     LK_CUDA(ctx, cudaMemsetAsync(ws.flags.p, 0, n * sizeof(int), s));
+    if (pk.n_items > 0)
+        LK_CUDA(ctx, cudaMemsetAsync(ws.item_fix.p, 0, pk.n_items * sizeof(unsigned long long), s));
     lk::launch_pair_frames(ws.tasks.p, n, ctx->d_aabb, s);
     const lk::SweepArgs a = sweep_args(ctx, ws, pk);
     if (pk.n_items > 0) {
@@ -356,7 +389,8 @@ lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStrea
             lk::launch_sweep_mixed(a, false, pk.n_acc_items, pk.n_items, ws.counters.p + 4,
                                    ctx->num_sms * lk::sweep_mixed_blocks_per_sm(false), s);
             if (ctx->opt.timing) LK_CUDA(ctx, record_event(ws.ev1, s));
-            lk::launch_sweep_careful(a, ctx->num_sms, s);
+            lk::launch_careful_chunks(a, ctx->num_sms * lk::careful_chunk_blocks_per_sm(), s);
+            lk::launch_sweep_careful(a, ctx->num_sms * lk::sweep_careful_blocks_per_sm(), s);
             lk::launch_near_fix(a, ctx->num_sms * 4, s);
         }
     }
@@ -365,6 +399,7 @@ lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStrea
     r.item_begin = ws.item_begin.p;
     r.partial = ws.partial.p;
     r.fix_acc = ws.fix_acc.p;
+    r.item_fix = ctx->opt.precision == LK_ALL_F64 ? nullptr : ws.item_fix.p;
     r.flags = ws.flags.p;
     r.n_tasks = n;
     r.int_tol = ctx->opt.int_tol;
@@ -434,12 +469,13 @@ extern "C" {
 void lk_default_options(lk_options* opt) {
     if (!opt) return;
     opt->precision = LK_MIXED;
-    opt->near_ratio = 4.0;
+    opt->near_ratio = 3.0;
     opt->int_tol = 0.1;
     opt->mem_budget = 0;
     opt->tile_rows = 0;
     opt->near_capacity = 1 << 20;
     opt->timing = 0;
+    opt->chunk_capacity = 1 << 20;
     opt->accurate_threshold = (int64_t)1 << 22;
 }
 
@@ -460,10 +496,10 @@ lk_status lk_create(lk_ctx** out, const void* vertices, lk_dtype vdtype, int64_t
     lk_options o;
     lk_default_options(&o);
     if (opt) o = *opt;
-    if (!(o.near_ratio >= 4.0) || !(o.int_tol > 0.0 && o.int_tol < 0.5) ||
+    if (!(o.near_ratio >= 3.0) || !(o.int_tol > 0.0 && o.int_tol < 0.5) ||
         (o.precision != LK_MIXED && o.precision != LK_ALL_F64) || o.tile_rows < 0 ||
-        o.near_capacity < 1 || o.accurate_threshold < 0)
-        return fail(nullptr, LK_ERR_ARG, "lk_create: invalid options (near_ratio >= 4, 0 < int_tol < 0.5)");
+        o.near_capacity < 1 || o.accurate_threshold < 0 || o.chunk_capacity < 1)
+        return fail(nullptr, LK_ERR_ARG, "lk_create: invalid options (near_ratio >= 3, 0 < int_tol < 0.5)");
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
     // Host copies for validation.
@@ -592,7 +628,7 @@ lk_status lk_verify(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, int
     if (st != LK_OK) return st;
     Packed pk;
     if ((st = pack_pairs(ctx, hp.data(), n_pairs, pk)) != LK_OK) return st;
-    if ((st = ensure_workspace(ctx, ctx->ws, n_pairs, pk.n_items)) != LK_OK) return st;
+    if ((st = ensure_workspace(ctx, ctx->ws, n_pairs, pk.n_items, pk.n_chunks)) != LK_OK) return st;
     if ((st = upload_packed(ctx, ctx->ws, pk, s)) != LK_OK) return st;
     if ((st = enqueue_verify(ctx, ctx->ws, pk, s)) != LK_OK) return st;
     note_stats(ctx, ctx->ws, pk, s);
@@ -617,9 +653,10 @@ lk_status lk_get_stats(lk_ctx* ctx, lk_stats* out) {
         LK_CUDA(ctx, cudaMemcpy(&ov, ctx->stats_overflow, sizeof ov, cudaMemcpyDeviceToHost));
         ctx->stats.fp64_pairs = (int64_t)std::accumulate(c.begin(), c.end(), 0ull);
         ctx->stats.near_overflow = (int64_t)ov;
-        unsigned int careful = 0;
-        LK_CUDA(ctx, cudaMemcpy(&careful, ctx->stats_careful, sizeof careful, cudaMemcpyDeviceToHost));
-        ctx->stats.careful_items = careful;
+        unsigned int u32[8] = {};
+        LK_CUDA(ctx, cudaMemcpy(u32, ctx->stats_careful, sizeof u32, cudaMemcpyDeviceToHost));
+        ctx->stats.careful_items = u32[0];
+        ctx->stats.careful_chunks = u32[6];
         ctx->stats.sweep_ms = -1.0;
         if (ctx->stats_ev0) {
             float ms = 0.0f;
@@ -656,7 +693,7 @@ lk_status lk_plan_create(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs
     lk_plan* plan = new lk_plan();
     plan->ctx = ctx;
     if ((st = pack_pairs(ctx, hp.data(), n_pairs, plan->pk)) != LK_OK ||
-        (st = ensure_workspace(ctx, plan->ws, n_pairs, plan->pk.n_items)) != LK_OK ||
+        (st = ensure_workspace(ctx, plan->ws, n_pairs, plan->pk.n_items, plan->pk.n_chunks)) != LK_OK ||
         (st = upload_packed(ctx, plan->ws, plan->pk, s)) != LK_OK) {
         lk_plan_destroy(plan);
         return st;
@@ -728,6 +765,7 @@ constexpr int64_t kNoallocMaxLoops = (int64_t)1 << 14;
 constexpr int64_t kNoallocMaxPairs = (int64_t)1 << 14;
 constexpr int64_t kNoallocMaxItems = (int64_t)1 << 18;
 constexpr int kNoallocNearCapacity = 1 << 16;
+constexpr int64_t kNoallocMaxChunks = (int64_t)1 << 16;
 constexpr int kNoallocMaxDevices = 64;
 
 std::mutex g_noalloc_mu;
@@ -833,6 +871,8 @@ extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, in
     bind(ws.item_task, (size_t)kNoallocMaxItems);
     bind(ws.partial, (size_t)kNoallocMaxItems);
     bind(ws.careful_items, (size_t)kNoallocMaxItems);
+    bind(ws.careful_chunks, (size_t)kNoallocMaxChunks);
+    bind(ws.item_fix, (size_t)kNoallocMaxItems);
     bind(ws.near_list, (size_t)kNoallocNearCapacity);
     bind(ws.fix_acc, (size_t)kNoallocMaxPairs);
     bind(ws.fp64_count, (size_t)kNoallocMaxPairs);
@@ -865,7 +905,7 @@ extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, in
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "lk_verify_noalloc: offsets");
     lk::launch_update(ctx.d_V, vsrc, vdtype == LK_F32 ? 0 : 1, 0, n_vertices, s);
     lk::launch_loop_aabb(ctx.d_V, ctx.d_offsets, n_loops, ctx.d_aabb, s);
-    if ((st = ensure_workspace(&ctx, ws, n_pairs, pk.n_items)) != LK_OK ||
+    if ((st = ensure_workspace(&ctx, ws, n_pairs, pk.n_items, pk.n_chunks)) != LK_OK ||
         (st = upload_packed(&ctx, ws, pk, s)) != LK_OK || (st = enqueue_verify(&ctx, ws, pk, s)) != LK_OK ||
         (st = copy_outputs(&ctx, ws, n_pairs, lk_out, raw_out, status_out, s)) != LK_OK)
         return fail(nullptr, st, ctx.err);
@@ -977,6 +1017,8 @@ size_t request_layout(const Packed& pk, int near_cap, Workspace* ws, uintptr_t b
     bind(ws->item_task, I);
     bind(ws->partial, I);
     bind(ws->careful_items, I);
+    bind(ws->careful_chunks, (size_t)std::max<int64_t>(1, std::min<int64_t>(pk.n_chunks, (int64_t)1 << 16)));
+    bind(ws->item_fix, I);
     bind(ws->near_list, (size_t)near_cap);
     bind(ws->fix_acc, P);
     bind(ws->fp64_count, P);
@@ -986,6 +1028,17 @@ size_t request_layout(const Packed& pk, int near_cap, Workspace* ws, uintptr_t b
     bind(ws->raw, P);
     bind(ws->status, P);
     return off;
+}
+
+size_t request_result_bytes(size_t P) {
+    return ((P * 4 + 255) & ~(size_t)255) + ((P * 8 + 255) & ~(size_t)255) + ((P * 4 + 255) & ~(size_t)255);
+}
+
+// Pinned host bytes of a request: its results, then its staged item tables.
+size_t request_host_bytes(const Packed& pk) {
+    const size_t P = pk.tasks.size();
+    return request_result_bytes(P) + P * sizeof(PairTask) + (P + 1) * sizeof(int64_t) +
+           (size_t)pk.n_items * sizeof(int32_t);
 }
 
 }  // namespace
@@ -1042,6 +1095,11 @@ lk::SweepArgs request_args(lk_ctx* ctx, Workspace& ws, const Packed& pk, int nea
     a.careful_counter = u32 + 1;
     a.near_count = u32 + 2;
     a.careful_items = ws.careful_items.p;
+    a.careful_chunks = ws.careful_chunks.p;
+    a.chunk_capacity = (int)std::min<size_t>(ws.careful_chunks.cap, (size_t)INT32_MAX);
+    a.chunk_count = u32 + 6;     // low half of counters[5]
+    a.chunk_counter = u32 + 7;   // high half of counters[5], low half of counters[6]
+    a.item_fix = ws.item_fix.p;
     a.near_list = ws.near_list.p;
     a.near_capacity = near_cap;
     a.fix_acc = ws.fix_acc.p;
@@ -1084,7 +1142,7 @@ lk_status admit(lk_server* s) {
             r->packed = true;
             Workspace probe;
             r->dev_bytes = request_layout(r->pk, s->opt.near_capacity, &probe, 0);
-            r->host_bytes = r->pk.tasks.size() * 16 + 1024;
+            r->host_bytes = request_host_bytes(r->pk);
         }
         if (!s->dev.alloc(r->dev_bytes, &r->dev_off)) break;           // memory-based admission
         if (!s->host.alloc(r->host_bytes, &r->host_off)) {
@@ -1098,13 +1156,26 @@ lk_status admit(lk_server* s) {
         r->h_raw = reinterpret_cast<double*>(hb + ((P * 4 + 255) & ~(size_t)255));
         r->h_status = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(r->h_raw) + ((P * 8 + 255) & ~(size_t)255));
         r->args = request_args(ctx, r->ws, r->pk, s->opt.near_capacity);
-        lk_status st = upload_packed(ctx, r->ws, r->pk, s->stream);
-        if (st != LK_OK) return srv_fail(s, st, ctx->err);
+        // Stage the item tables in pinned memory so that their upload is truly
+        // asynchronous (a pageable source would make the copy wait for the
+        // waves already queued on the stream, serialising host and device).
+        unsigned char* tb = hb + request_result_bytes(P);
+        const size_t tbytes = P * sizeof(PairTask), bbytes = (P + 1) * sizeof(int64_t),
+                     ibytes = (size_t)r->pk.n_items * sizeof(int32_t);
+        std::memcpy(tb, r->pk.tasks.data(), tbytes);
+        std::memcpy(tb + tbytes, r->pk.item_begin.data(), bbytes);
+        if (ibytes) std::memcpy(tb + tbytes + bbytes, r->pk.item_task.data(), ibytes);
+        LK_SRV_CUDA(s, cudaMemcpyAsync(r->ws.tasks.p, tb, tbytes, cudaMemcpyHostToDevice, s->stream));
+        LK_SRV_CUDA(s, cudaMemcpyAsync(r->ws.item_begin.p, tb + tbytes, bbytes, cudaMemcpyHostToDevice, s->stream));
+        if (ibytes)
+            LK_SRV_CUDA(s, cudaMemcpyAsync(r->ws.item_task.p, tb + tbytes + bbytes, ibytes, cudaMemcpyHostToDevice,
+                                           s->stream));
         const int64_t n = (int64_t)P;
         LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.counters.p, 0, 8 * sizeof(unsigned long long), s->stream));
         LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.fix_acc.p, 0, n * sizeof(unsigned long long), s->stream));
         LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.fp64_count.p, 0, n * sizeof(unsigned long long), s->stream));
         LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.flags.p, 0, n * sizeof(int), s->stream));
+        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.item_fix.p, 0, r->ws.item_fix.cap * sizeof(unsigned long long), s->stream));
         lk::launch_pair_frames(r->ws.tasks.p, n, ctx->d_aabb, s->stream);
         r->state = kRunning;
         r->next_item = 0;
@@ -1168,13 +1239,15 @@ lk_status launch_wave(lk_server* s) {
     lk::launch_wave(s->d_segs[slot] + n_acc, n_fast, fast_items, false, cnt + 1,
                     s->num_sms * lk::wave_blocks_per_sm(false), st);
     for (Request* r : completing) {
-        lk::launch_sweep_careful(r->args, s->num_sms, st);
+        lk::launch_careful_chunks(r->args, s->num_sms * lk::careful_chunk_blocks_per_sm(), st);
+        lk::launch_sweep_careful(r->args, s->num_sms * lk::sweep_careful_blocks_per_sm(), st);
         lk::launch_near_fix(r->args, s->num_sms * 4, st);
         lk::ReduceArgs ra{};
         ra.tasks = r->ws.tasks.p;
         ra.item_begin = r->ws.item_begin.p;
         ra.partial = r->ws.partial.p;
         ra.fix_acc = r->ws.fix_acc.p;
+        ra.item_fix = r->ws.item_fix.p;
         ra.flags = r->ws.flags.p;
         ra.n_tasks = (int64_t)r->pk.tasks.size();
         ra.int_tol = r->ctx->opt.int_tol;
@@ -1209,7 +1282,7 @@ void lk_server_default_options(lk_server_options* o) {
     if (!o) return;
     o->max_requests = 64;
     o->arena_bytes = (size_t)1 << 30;
-    o->host_bytes = (size_t)64 << 20;
+    o->host_bytes = (size_t)256 << 20;
     o->wave_items = 16384;
     o->near_capacity = 4096;
     o->max_queue = 1 << 16;
@@ -1278,7 +1351,7 @@ lk_status lk_server_submit(lk_server* s, lk_ctx* ctx, const int32_t* loop_pairs,
     r->packed = true;
     Workspace probe;
     r->dev_bytes = request_layout(r->pk, s->opt.near_capacity, &probe, 0);
-    r->host_bytes = r->pk.tasks.size() * 16 + 1024;
+    r->host_bytes = request_host_bytes(r->pk);
     if (Arena::round(r->dev_bytes) > s->opt.arena_bytes || Arena::round(r->host_bytes) > s->opt.host_bytes) {
         delete r;
         return srv_fail(s, LK_ERR_OOM, "lk_server_submit: request larger than the server's arena");

@@ -29,6 +29,11 @@ constexpr int kF64TileCols = 32;
 // which threads add them.
 constexpr double kFixScale = 274877906944.0;  // 2^38
 
+// Careful-pass results of single chunks are added to their item as
+// fixed-point integers of 2^-32 rad (order-independent; an item holds at most
+// a few thousand chunks, so the sum cannot overflow).
+constexpr double kChunkFixScale = 4294967296.0;  // 2^32
+
 // Per-pair flag bits.
 constexpr int kFlagIntersect = 1;
 
@@ -59,6 +64,13 @@ struct NearEntry {
     int32_t pad;
 };
 
+// A 32-row chunk handed from the bulk sweep to the careful pass.
+struct CarefulChunk {
+    int64_t item;
+    int32_t chunk;   // chunk index within the item
+    int32_t pad;
+};
+
 struct SweepArgs {
     const PairTask* tasks;
     const int64_t* item_begin;     // [n_tasks+1] first item of each task
@@ -69,13 +81,19 @@ struct SweepArgs {
     unsigned long long* item_counter;
     int64_t* careful_items;        // [n_items] items handed to the careful pass
     unsigned int* careful_count;   // [1] entries of careful_items
-    unsigned int* careful_counter; // [1] work counter of the careful pass
+    unsigned int* careful_counter; // [1] work counter of the careful pass (fast items);
+                                   // careful_counter + 2: accurate items
     NearEntry* near_list;
     unsigned int* near_count;
     int near_capacity;
     unsigned long long* fix_acc;   // [n_tasks] fixed-point radians of FP64 recomputes
     unsigned long long* fp64_count;// [n_tasks] segment pairs recomputed in FP64
     unsigned long long* overflow;  // [1] recomputes evaluated in place (list full)
+    CarefulChunk* careful_chunks;  // chunks handed over by the bulk sweep
+    unsigned int* chunk_count;     // [1] entries of careful_chunks (may exceed capacity)
+    unsigned int* chunk_counter;   // [2] work counters of the chunk pass (fast, accurate)
+    int chunk_capacity;
+    unsigned long long* item_fix;  // [n_items] fixed-point 2^-32 rad: careful chunk sums
     int* flags;                    // [n_tasks] kFlag* bits
     float near_ratio_sq;           // tau^2
 };
@@ -91,6 +109,7 @@ struct ReduceArgs {
     const PairTask* tasks;
     const int64_t* item_begin;
     const double* partial;
+    const unsigned long long* item_fix;   // may be null
     const unsigned long long* fix_acc;
     const int* flags;
     int64_t n_tasks;
@@ -108,6 +127,8 @@ void launch_sweep_mixed(const SweepArgs& a, bool accurate, int64_t item_lo, int6
                         unsigned long long* counter, int grid, cudaStream_t s);
 void launch_sweep_f64(const SweepArgs& a, int grid, cudaStream_t s);
 void launch_sweep_careful(const SweepArgs& a, int grid, cudaStream_t s);
+void launch_careful_chunks(const SweepArgs& a, int grid, cudaStream_t s);
+int careful_chunk_blocks_per_sm();
 void launch_near_fix(const SweepArgs& a, int grid, cudaStream_t s);
 void launch_wave(const WaveSeg* segs, int n_segs, int64_t n_items, bool accurate,
                  unsigned long long* counter, int grid, cudaStream_t s);
@@ -116,5 +137,6 @@ void launch_reduce(const ReduceArgs& a, cudaStream_t s);
 void launch_update(Vtx* V, const void* data, int dtype, int is_delta, int64_t n, cudaStream_t s);
 int sweep_mixed_blocks_per_sm(bool accurate);
 int sweep_f64_blocks_per_sm();
+int sweep_careful_blocks_per_sm();
 
 }  // namespace lk

@@ -44,7 +44,8 @@ class lk_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("near_ratio", ctypes.c_double),
                 ("int_tol", ctypes.c_double), ("mem_budget", ctypes.c_size_t),
                 ("tile_rows", ctypes.c_int), ("near_capacity", ctypes.c_int),
-                ("timing", ctypes.c_int), ("accurate_threshold", ctypes.c_int64)]
+                ("timing", ctypes.c_int), ("chunk_capacity", ctypes.c_int),
+                ("accurate_threshold", ctypes.c_int64)]
 
 
 class lk_stats(ctypes.Structure):
@@ -52,7 +53,7 @@ class lk_stats(ctypes.Structure):
                 ("segment_pairs", ctypes.c_int64), ("fp64_pairs", ctypes.c_int64),
                 ("near_overflow", ctypes.c_int64), ("tile_rows", ctypes.c_int32),
                 ("tile_cols", ctypes.c_int32), ("careful_items", ctypes.c_int64),
-                ("sweep_ms", ctypes.c_double)]
+                ("sweep_ms", ctypes.c_double), ("careful_chunks", ctypes.c_int64)]
 
 
 class lk_server_options(ctypes.Structure):

@@ -1,0 +1,117 @@
+"""Open-loop serving driver over the library's continuous-batching server.
+
+Requests arrive as a Poisson process; each asks to verify a window of
+1k-20k candidate pairs of one of several resident chainmail piles (the
+per-frame verification of a running simulation).  Between requests a pile
+receives a small displacement (lk_update) when none of its requests is in
+flight.  Latency is measured from a request's scheduled arrival to the moment
+lk_server_poll hands its results to the host.  All linking-number work runs in
+the library; this module only schedules submissions and reads clocks.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import lk
+from . import workloads as W
+
+
+@dataclass
+class Scene:
+    geometry: W.Geometry
+    ctx: int
+    delta_pos: object      # device tensors
+    delta_neg: object
+    flip: bool = False
+    in_flight: int = 0
+
+
+def make_scenes(seed=5, n_scenes=6, min_rings=500, max_rings=14000, sigma=1e-3, stream=None):
+    """Resident chainmail piles with log-uniform ring counts and 64-256 segments per ring.
+    The per-step displacements live in device memory, as a simulation's would."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    scenes = []
+    for k in range(n_scenes):
+        g = W.serving_pile(int(rng.integers(1 << 30)), min_rings, max_rings)
+        ctx = lk.lk_create(g.vertices, g.offsets, None, stream)
+        d = rng.normal(scale=sigma, size=g.vertices.shape).astype(g.vertices.dtype)
+        scenes.append(Scene(g, ctx, torch.from_numpy(d).cuda(), torch.from_numpy(np.ascontiguousarray(-d)).cuda()))
+    return scenes
+
+
+def request_plan(scenes, n_requests, seed=0, min_pairs=1000, max_pairs=20000):
+    """(scene index, pair window) for each request; window sizes log-uniform."""
+    rng = np.random.default_rng(seed)
+    plan = []
+    for _ in range(n_requests):
+        k = int(rng.integers(len(scenes)))
+        pairs = scenes[k].geometry.pairs
+        want = int(np.exp(rng.uniform(np.log(min_pairs), np.log(max_pairs))))
+        m = min(want, pairs.shape[0])
+        lo = int(rng.integers(0, pairs.shape[0] - m + 1))
+        plan.append((k, np.ascontiguousarray(pairs[lo:lo + m])))
+    return plan
+
+
+def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0):
+    """Serve `plan`; arrivals are Poisson at rate_per_s (None: all at t = 0).
+    Returns per-request latencies (s), the wall time, and the number of pair
+    results whose status was not LK_OK."""
+    rng = np.random.default_rng(seed)
+    n = len(plan)
+    if rate_per_s is None:
+        arrivals = np.zeros(n)
+    else:
+        arrivals = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+    stream = lk.lk_server_stream(srv)
+    status = np.zeros(max(p.shape[0] for _, p in plan), np.int32)
+    bad = 0
+    pending = {}          # ticket -> (request index, scene index)
+    lat = np.zeros(n)
+    nxt = 0
+    done = 0
+    t0 = time.perf_counter()
+    while done < n:
+        now = time.perf_counter() - t0
+        if now > timeout_s:
+            raise TimeoutError("serving run exceeded %.0f s" % timeout_s)
+        while nxt < n and arrivals[nxt] <= now:
+            k, pairs = plan[nxt]
+            sc = scenes[k]
+            if update and sc.in_flight == 0:
+                lk.lk_update(sc.ctx, sc.delta_neg if sc.flip else sc.delta_pos, True, stream)
+                sc.flip = not sc.flip
+            t = lk.lk_server_submit(srv, sc.ctx, pairs)
+            sc.in_flight += 1
+            pending[t] = (nxt, k)
+            nxt += 1
+        lk.lk_server_step(srv, wait=False)
+        for t in list(pending):
+            if lk.lk_server_poll(srv, t, None, None, status):
+                i, k = pending.pop(t)
+                bad += int(np.count_nonzero(status[:plan[i][1].shape[0]]))
+                lat[i] = (time.perf_counter() - t0) - arrivals[i]
+                scenes[k].in_flight -= 1
+                done += 1
+        if not pending and nxt < n:
+            wait = arrivals[nxt] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(min(wait, 0.001))
+    wall = time.perf_counter() - t0
+    return lat, wall, bad
+
+
+def plan_sizes(scenes, plan):
+    pairs = np.array([p.shape[0] for _, p in plan], dtype=np.int64)
+    sps = np.array([scenes[k].geometry.segment_pairs(p) for k, p in plan], dtype=np.int64)
+    return pairs, sps
+
+
+def close(scenes):
+    for sc in scenes:
+        lk.lk_destroy(sc.ctx)

@@ -47,7 +47,7 @@ def test_binding_covers_every_declared_symbol():
 def test_default_options(lib):
     o = lk.lk_default_options()
     assert o.precision == lk.LK_MIXED
-    assert o.near_ratio == 4.0
+    assert o.near_ratio == 3.0
     assert o.int_tol == 0.1
     assert o.near_capacity == 1 << 20
 
@@ -67,7 +67,7 @@ def test_create_rejects_bad_geometry_before_device_work(lib):
     bad[3, 1] = np.nan
     assert _create_status(bad, np.array([0, 5, 10], np.int64)) == lk.LK_ERR_ARG
     o = lk.lk_default_options()
-    o.near_ratio = 3.0
+    o.near_ratio = 2.5
     assert _create_status(v, np.array([0, 5, 10], np.int64), o) == lk.LK_ERR_ARG
 
 

@@ -217,6 +217,11 @@ def test_near_segments_take_the_fp64_path():
     assert st[0] == 0 and lk_o[0] == O.round_lk(ref)[0]
     assert abs(raw[0] - ref[0]) <= RAW_TOL
     assert s["fp64_pairs"] > 0
+    assert s["careful_chunks"] > 0 and s["careful_items"] == 0
+    # a one-entry chunk list hands whole items to the careful pass instead
+    lk3, raw3, st3, s3 = run(g, stats=True, chunk_capacity=1)
+    assert s3["careful_items"] > 0
+    assert st3[0] == 0 and lk3[0] == lk_o[0] and abs(raw3[0] - raw[0]) <= 1e-9
     # a tiny list forces the in-place FP64 evaluation of the overflow
     lk2, raw2, st2, s2 = run(g, stats=True, near_capacity=3)
     assert s2["near_overflow"] > 0

@@ -98,8 +98,17 @@ def test_results_alone_and_in_the_mix_are_identical():
 def test_admission_waits_for_arena_memory():
     g = W.chainmail(seed=7, rows=8, cols=16)
     ctx = lk.lk_create(g.vertices, g.offsets)
+    # measure one request's arena footprint, then give the server room for
+    # one such request at a time
+    probe = lk.lk_server_create(None)
+    t = lk.lk_server_submit(probe, ctx, g.pairs)
+    lk.lk_server_step(probe)
+    one = lk.lk_server_get_stats(probe)["arena_used"]
+    drain(probe, [t], {t: g.pairs.shape[0]})
+    lk.lk_server_destroy(probe)
+    assert one > 0
     o = lk.lk_server_default_options()
-    o.arena_bytes = 300 << 10                # room for one request of this size at a time
+    o.arena_bytes = int(one * 1.5)
     o.wave_items = 256
     srv = lk.lk_server_create(o)
     try:
