@@ -181,6 +181,27 @@ lk_status lk_plan_run(lk_plan* plan, int32_t* lk_out, double* raw_out, int32_t* 
 void lk_plan_destroy(lk_plan* plan);
 
 /*
+ * Autotuner for the work split (the batching of Algorithm 1's loop over P
+ * into work items; the paper launches one kernel per pair, Sec. 3.4).
+ * For each size class present in loop_pairs -- a class is the pair
+ * (ceil(log2 N_rows), ceil(log2 N_cols)) of the longer and shorter loop --
+ * times the mixed-precision verify of up to 4096 of that class's pairs
+ * (at most 2^31 segment pairs) at each candidate work-item height
+ * (32 ... 65536 row segments) with CUDA events, and records the fastest in the
+ * context.  Later verifies and plans of pairs in a tuned class use it unless
+ * options.tile_rows is set.  The split changes the order of the FP64 sums, not
+ * which segment pairs are evaluated: results agree with the untuned ones to
+ * rounding, and are deterministic for a given table.  Synchronises
+ * cuda_stream.  Errors: LK_ERR_ARG, LK_ERR_OOM, LK_ERR_CUDA.
+ */
+lk_status lk_autotune(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, void* cuda_stream);
+/* The tuning table: entries[3k..3k+2] = (row class, column class, rows per
+ * item).  lk_tune_get writes at most `capacity` entries and the total count to
+ * *n_entries; lk_tune_set replaces the table (e.g. with one saved for this GPU). */
+lk_status lk_tune_get(lk_ctx* ctx, int32_t* entries, int64_t capacity, int64_t* n_entries);
+lk_status lk_tune_set(lk_ctx* ctx, const int32_t* entries, int64_t n_entries);
+
+/*
  * Serving: continuous batching of verify requests over resident geometry
  * (the per-frame verification of Sec. 5's simulation examples, as a service).
  * A server owns a device arena of arena_bytes (requests are admitted only

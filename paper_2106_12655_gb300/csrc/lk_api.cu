@@ -146,6 +146,7 @@ struct lk_ctx {
     const unsigned int* stats_careful = nullptr;
     cudaEvent_t stats_ev0 = nullptr, stats_ev1 = nullptr;
     cudaStream_t stats_stream = nullptr;
+    std::map<uint32_t, int> tune;   // size class -> tile rows chosen by lk_autotune
     std::string err;
 };
 
@@ -176,6 +177,16 @@ lk_status cuda_fail(lk_ctx* ctx, cudaError_t e, const char* where) {
         cudaError_t e_ = (call);                            \
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
     } while (0)
+
+// Size class of a pair for tuning: ceil(log2) of its row and column loop sizes.
+uint32_t size_class(int64_t n_rows, int64_t n_cols) {
+    auto clog2 = [](int64_t v) {
+        uint32_t b = 0;
+        while (((int64_t)1 << b) < v) ++b;
+        return b;
+    };
+    return (clog2(n_rows) << 8) | clog2(n_cols);
+}
 
 int default_tile_rows(int64_t n_rows, int64_t n_cols, int tile_cols, int user_rows) {
     if (user_rows > 0) return user_rows;
@@ -221,7 +232,12 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
         t.col_base = ctx->h_offsets[t.col_loop];
         t.n_rows = (int32_t)(a_rows ? na : nb);
         t.n_cols = (int32_t)(a_rows ? nb : na);
-        t.tile_rows = default_tile_rows(t.n_rows, t.n_cols, tile_cols, ctx->opt.tile_rows);
+        int rows = ctx->opt.tile_rows;
+        if (rows <= 0 && !f64) {
+            auto it = ctx->tune.find(size_class(t.n_rows, t.n_cols));
+            if (it != ctx->tune.end()) rows = it->second;
+        }
+        t.tile_rows = default_tile_rows(t.n_rows, t.n_cols, tile_cols, rows);
         t.col_tiles = (t.n_cols + tile_cols - 1) / tile_cols;
         const int64_t row_tiles = (t.n_rows + t.tile_rows - 1) / t.tile_rows;
         items[(size_t)p] = (int64_t)t.col_tiles * row_tiles;
@@ -1424,6 +1440,131 @@ void lk_server_destroy(lk_server* s) {
     if (s->h_arena) cudaFreeHost(s->h_arena);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Autotuner: rows per work item, per size class.
+//
+// The tile width is fixed by the kernel (128 column segments per warp); what
+// is tuned is how many row segments a work item covers, which trades the
+// per-item set-up (column staging, pair look-up, one partial) against the
+// tail of the persistent grid and, for huge pairs, the number of partials.
+// For every size class present in the given pair list the tuner times the
+// mixed-precision verify of (a sample of) that class's pairs at each
+// candidate height with CUDA events and keeps the fastest.  The table only
+// changes the split, never the segment pairs evaluated; a pair's result is
+// deterministic for a given table.
+namespace {
+
+const int kTuneCandidates[] = {32, 64, 128, 256, 512, 1024, 2048, 4096, 16384, 65536};
+constexpr int64_t kTuneMaxSegmentPairs = (int64_t)2 << 30;   // per timed sample
+constexpr int kTuneMaxPairs = 4096;
+
+lk_status time_verify(lk_ctx* ctx, const std::vector<int32_t>& pairs, int tile_rows, cudaStream_t s,
+                      cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+    const int saved = ctx->opt.tile_rows;
+    ctx->opt.tile_rows = tile_rows;
+    Packed pk;
+    lk_status st = pack_pairs(ctx, pairs.data(), (int64_t)(pairs.size() / 2), pk);
+    ctx->opt.tile_rows = saved;
+    if (st != LK_OK) return st;
+    if ((st = ensure_workspace(ctx, ctx->ws, (int64_t)pk.tasks.size(), pk.n_items, pk.n_chunks)) != LK_OK) return st;
+    if ((st = upload_packed(ctx, ctx->ws, pk, s)) != LK_OK) return st;
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        LK_CUDA(ctx, cudaEventRecord(e0, s));
+        if ((st = enqueue_verify(ctx, ctx->ws, pk, s)) != LK_OK) return st;
+        LK_CUDA(ctx, cudaEventRecord(e1, s));
+        LK_CUDA(ctx, cudaEventSynchronize(e1));
+        float m = 0.0f;
+        LK_CUDA(ctx, cudaEventElapsedTime(&m, e0, e1));
+        if (rep > 0) best = std::min(best, m);      // the first run warms caches
+    }
+    *ms = best;
+    return LK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lk_status lk_autotune(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, void* cuda_stream) {
+    if (!ctx) return fail(nullptr, LK_ERR_ARG, "lk_autotune: NULL context");
+    if (n_pairs < 0 || (n_pairs > 0 && !loop_pairs)) return fail(ctx, LK_ERR_ARG, "lk_autotune: invalid pairs");
+    if (ctx->opt.precision != LK_MIXED) return LK_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    std::vector<int32_t> hp;
+    lk_status st = get_pairs_on_host(ctx, loop_pairs, n_pairs, s, hp);
+    if (st != LK_OK) return st;
+    // group valid pairs by size class
+    std::map<uint32_t, std::vector<int32_t>> groups;
+    std::map<uint32_t, int64_t> group_sp, group_rows;
+    for (int64_t p = 0; p < n_pairs; ++p) {
+        const int32_t a = hp[2 * p], b = hp[2 * p + 1];
+        if (a < 0 || b < 0 || a >= ctx->n_loops || b >= ctx->n_loops || a == b) continue;
+        const int64_t na = ctx->h_offsets[a + 1] - ctx->h_offsets[a];
+        const int64_t nb = ctx->h_offsets[b + 1] - ctx->h_offsets[b];
+        const int64_t nr = std::max(na, nb), nc = std::min(na, nb);
+        const uint32_t key = size_class(nr, nc);
+        auto& g = groups[key];
+        if ((int64_t)g.size() / 2 >= kTuneMaxPairs || group_sp[key] + nr * nc > kTuneMaxSegmentPairs) continue;
+        g.push_back(a);
+        g.push_back(b);
+        group_sp[key] += nr * nc;
+        group_rows[key] = std::max(group_rows[key], nr);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LK_CUDA(ctx, cudaEventCreate(&e0));
+    LK_CUDA(ctx, cudaEventCreate(&e1));
+    for (auto& kv : groups) {
+        if (kv.second.empty()) continue;
+        const int64_t max_rows = group_rows[kv.first];
+        int best_rows = 0;
+        float best_ms = 1e30f;
+        for (int cand : kTuneCandidates) {
+            if (cand > 2 * max_rows && cand != kTuneCandidates[0]) break;
+            float ms = 0.0f;
+            if ((st = time_verify(ctx, kv.second, cand, s, e0, e1, &ms)) != LK_OK) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_rows = cand;
+            }
+        }
+        if (st != LK_OK) break;
+        if (best_rows > 0) ctx->tune[kv.first] = best_rows;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+lk_status lk_tune_get(lk_ctx* ctx, int32_t* entries, int64_t capacity, int64_t* n_entries) {
+    if (!ctx || !n_entries || (capacity > 0 && !entries)) return fail(ctx, LK_ERR_ARG, "lk_tune_get: invalid arguments");
+    *n_entries = (int64_t)ctx->tune.size();
+    int64_t k = 0;
+    for (auto& kv : ctx->tune) {
+        if (k >= capacity) break;
+        entries[3 * k + 0] = (int32_t)(kv.first >> 8);
+        entries[3 * k + 1] = (int32_t)(kv.first & 0xff);
+        entries[3 * k + 2] = kv.second;
+        ++k;
+    }
+    return LK_OK;
+}
+
+lk_status lk_tune_set(lk_ctx* ctx, const int32_t* entries, int64_t n_entries) {
+    if (!ctx || n_entries < 0 || (n_entries > 0 && !entries)) return fail(ctx, LK_ERR_ARG, "lk_tune_set: invalid arguments");
+    for (int64_t k = 0; k < n_entries; ++k) {
+        const int32_t rb = entries[3 * k], cb = entries[3 * k + 1], rows = entries[3 * k + 2];
+        if (rb < 0 || rb > 40 || cb < 0 || cb > 40 || rows < 1)
+            return fail(ctx, LK_ERR_ARG, "lk_tune_set: invalid entry");
+    }
+    ctx->tune.clear();
+    for (int64_t k = 0; k < n_entries; ++k)
+        ctx->tune[((uint32_t)entries[3 * k] << 8) | (uint32_t)entries[3 * k + 1]] = entries[3 * k + 2];
+    return LK_OK;
 }
 
 }  // extern "C"

@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "LK_OK", 1: "LK_ERR_ARG", 2: "LK_ERR_ZERO_SEGMENT", 3: "LK_ER
 
 EXPORTED = ["lk_default_options", "lk_create", "lk_update", "lk_verify", "lk_sync", "lk_get_stats",
             "lk_destroy", "lk_last_error", "lk_plan_create", "lk_plan_run", "lk_plan_destroy",
-            "lk_verify_noalloc", "lk_server_default_options", "lk_server_create", "lk_server_stream",
+            "lk_verify_noalloc", "lk_autotune", "lk_tune_get", "lk_tune_set", "lk_server_default_options", "lk_server_create", "lk_server_stream",
             "lk_server_submit", "lk_server_step", "lk_server_poll", "lk_server_get_stats",
             "lk_server_last_error", "lk_server_destroy"]
 
@@ -132,6 +132,12 @@ def load(path: str | None = None):
     lib.lk_server_last_error.argtypes = [vp]
     lib.lk_server_destroy.restype = None
     lib.lk_server_destroy.argtypes = [vp]
+    lib.lk_autotune.restype = ctypes.c_int
+    lib.lk_autotune.argtypes = [vp, i32p, i64, vp]
+    lib.lk_tune_get.restype = ctypes.c_int
+    lib.lk_tune_get.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)]
+    lib.lk_tune_set.restype = ctypes.c_int
+    lib.lk_tune_set.argtypes = [vp, vp, i64]
     lib.lk_verify_noalloc.restype = ctypes.c_int
     lib.lk_verify_noalloc.argtypes = [vp, ctypes.c_int, i64, vp, i64, i32p, i64, vp, vp, vp, vp]
     _lib = lib
@@ -267,6 +273,27 @@ def lk_verify_noalloc(vertices, loop_offsets, loop_pairs, lk_out=None, raw_out=N
                                     _ptr(loop_offsets), int(loop_offsets.shape[0]) - 1, _ptr(loop_pairs),
                                     int(loop_pairs.shape[0]), _ptr(lk_out), _ptr(raw_out), _ptr(status_out),
                                     _stream(stream)))
+
+
+def lk_autotune(ctx, loop_pairs, stream=None):
+    if str(loop_pairs.dtype).split(".")[-1] != "int32":
+        raise TypeError("loop_pairs must be int32")
+    _check(load().lk_autotune(ctx, _ptr(loop_pairs), int(loop_pairs.shape[0]), _stream(stream)), ctx)
+
+
+def lk_tune_get(ctx) -> np.ndarray:
+    """The tuning table as an int32 [n, 3] array (row class, column class, rows per item)."""
+    n = ctypes.c_int64()
+    _check(load().lk_tune_get(ctx, None, 0, ctypes.byref(n)), ctx)
+    out = np.zeros((n.value, 3), np.int32)
+    if n.value:
+        _check(load().lk_tune_get(ctx, out.ctypes.data, n.value, ctypes.byref(n)), ctx)
+    return out
+
+
+def lk_tune_set(ctx, entries):
+    e = np.ascontiguousarray(np.asarray(entries, np.int32).reshape(-1, 3))
+    _check(load().lk_tune_set(ctx, e.ctypes.data if e.size else None, e.shape[0]), ctx)
 
 
 def _check_srv(status, srv):

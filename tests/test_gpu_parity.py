@@ -298,3 +298,36 @@ def test_update_matches_fresh_context():
     assert np.abs(raw - fresh[1]).max() <= 1e-9
     ref = O.link_pairs(moved.vertices, moved.offsets, moved.pairs)
     assert np.abs(raw - ref).max() <= RAW_TOL
+
+
+def test_autotune_changes_only_the_split(tmp_path):
+    from paper_2106_12655_gb300 import tuning
+
+    g = W.chainmail(rows=12, cols=24)
+    stream = torch.cuda.current_stream()
+    ctx = lk.lk_create(g.vertices, g.offsets, None, stream)
+    try:
+        n = g.pairs.shape[0]
+        base = np.zeros(n, np.int32), np.zeros(n), np.zeros(n, np.int32)
+        lk.lk_verify(ctx, g.pairs, *base)
+        lk.lk_autotune(ctx, g.pairs, stream)
+        table = lk.lk_tune_get(ctx)
+        assert table.shape[0] >= 1 and np.all(table[:, 2] >= 32)
+        tuned = np.zeros(n, np.int32), np.zeros(n), np.zeros(n, np.int32)
+        lk.lk_verify(ctx, g.pairs, *tuned)
+        assert np.array_equal(tuned[0], base[0]) and np.array_equal(tuned[2], base[2])
+        assert np.max(np.abs(tuned[1] - base[1])) <= 1e-9
+        # the cache round-trips the table
+        path = str(tmp_path / "tune.json")
+        tuning.save(ctx, "test-gpu", path)
+        lk.lk_tune_set(ctx, np.zeros((0, 3), np.int32))
+        assert lk.lk_tune_get(ctx).shape[0] == 0
+        assert tuning.restore(ctx, "test-gpu", path)
+        assert np.array_equal(lk.lk_tune_get(ctx), table)
+        # a forced split gives the same answer too
+        forced = np.zeros(n, np.int32), np.zeros(n), np.zeros(n, np.int32)
+        lk.lk_tune_set(ctx, np.array([[r, c, 64] for r, c, _ in table], np.int32))
+        lk.lk_verify(ctx, g.pairs, *forced)
+        assert np.max(np.abs(forced[1] - base[1])) <= 1e-9
+    finally:
+        lk.lk_destroy(ctx)
