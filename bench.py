@@ -268,9 +268,9 @@ def run_ours(args):
     stats = lk.lk_get_stats(ctx)
     total_ms = sum(step_ms)
     if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        from paper_2106_12655_gb300 import multigpu as MG
+
+        total_ms = MG.max_over_ranks(total_ms, dist, dev)
     value = world * sps_per_step * args.steps / (total_ms / 1e3)
     lk_host = lk_o.cpu().numpy()
     raw_host = raw_o.cpu().numpy()

@@ -181,6 +181,25 @@ lk_status lk_plan_run(lk_plan* plan, int32_t* lk_out, double* raw_out, int32_t* 
 void lk_plan_destroy(lk_plan* plan);
 
 /*
+ * Early-exit verification of a certificate (Sec. 3.1, "Fast Verification":
+ * exit as soon as any linking number differs from the input).  Verifies the
+ * pairs in input order, in batches of at most batch_segment_pairs segment
+ * pairs (0 = 2^30; every batch holds at least one pair), and after each batch
+ * compares the rounded linking numbers with expected[] ([n_pairs] int32, host
+ * or device).  A pair whose status is not LK_OK also counts as a mismatch.
+ *  *first_mismatch : the smallest mismatching index of the first batch that
+ *                    has one, or -1 if every pair matches.
+ *  *n_checked      : pairs verified before stopping (a prefix of the list).
+ * lk_out / raw_out / status_out (may be NULL) receive the results of the
+ * checked prefix; entries past it are left untouched.  Synchronises
+ * cuda_stream after each batch.  Errors: as lk_verify.
+ */
+lk_status lk_verify_expected(lk_ctx* ctx, const int32_t* loop_pairs, const int32_t* expected,
+                             int64_t n_pairs, int64_t batch_segment_pairs, int64_t* first_mismatch,
+                             int64_t* n_checked, int32_t* lk_out, double* raw_out, int32_t* status_out,
+                             void* cuda_stream);
+
+/*
  * Autotuner for the work split (the batching of Algorithm 1's loop over P
  * into work items; the paper launches one kernel per pair, Sec. 3.4).
  * For each size class present in loop_pairs -- a class is the pair

@@ -1568,3 +1568,68 @@ lk_status lk_tune_set(lk_ctx* ctx, const int32_t* entries, int64_t n_entries) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Early-exit verification against an expected certificate.
+extern "C" lk_status lk_verify_expected(lk_ctx* ctx, const int32_t* loop_pairs, const int32_t* expected,
+                                        int64_t n_pairs, int64_t batch_segment_pairs, int64_t* first_mismatch,
+                                        int64_t* n_checked, int32_t* lk_out, double* raw_out,
+                                        int32_t* status_out, void* cuda_stream) {
+    if (!ctx) return fail(nullptr, LK_ERR_ARG, "lk_verify_expected: NULL context");
+    if (n_pairs < 0 || (n_pairs > 0 && (!loop_pairs || !expected)) || !first_mismatch || !n_checked ||
+        batch_segment_pairs < 0 || n_pairs > INT32_MAX)
+        return fail(ctx, LK_ERR_ARG, "lk_verify_expected: invalid arguments");
+    *first_mismatch = -1;
+    *n_checked = 0;
+    if (n_pairs == 0) return LK_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    std::vector<int32_t> hp, he((size_t)n_pairs);
+    lk_status st = get_pairs_on_host(ctx, loop_pairs, n_pairs, s, hp);
+    if (st != LK_OK) return st;
+    if (is_device_ptr(expected)) {
+        LK_CUDA(ctx, cudaMemcpyAsync(he.data(), expected, n_pairs * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LK_CUDA(ctx, cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(he.data(), expected, n_pairs * sizeof(int32_t));
+    }
+    const int64_t budget = batch_segment_pairs > 0 ? batch_segment_pairs : ((int64_t)1 << 30);
+    std::vector<int32_t> blk, bst;
+    int64_t b0 = 0;
+    while (b0 < n_pairs) {
+        // next batch: at least one pair, up to the segment-pair budget
+        int64_t b1 = b0, sp = 0;
+        while (b1 < n_pairs) {
+            const int32_t a = hp[2 * b1], b = hp[2 * b1 + 1];
+            int64_t c = 0;
+            if (a >= 0 && b >= 0 && a < ctx->n_loops && b < ctx->n_loops)
+                c = (ctx->h_offsets[a + 1] - ctx->h_offsets[a]) * (ctx->h_offsets[b + 1] - ctx->h_offsets[b]);
+            if (b1 > b0 && sp + c > budget) break;
+            sp += c;
+            ++b1;
+        }
+        const int64_t m = b1 - b0;
+        Packed pk;
+        if ((st = pack_pairs(ctx, hp.data() + 2 * b0, m, pk)) != LK_OK) return st;
+        if ((st = ensure_workspace(ctx, ctx->ws, m, pk.n_items, pk.n_chunks)) != LK_OK) return st;
+        if ((st = upload_packed(ctx, ctx->ws, pk, s)) != LK_OK) return st;
+        if ((st = enqueue_verify(ctx, ctx->ws, pk, s)) != LK_OK) return st;
+        note_stats(ctx, ctx->ws, pk, s);
+        if ((st = copy_outputs(ctx, ctx->ws, m, lk_out ? lk_out + b0 : nullptr, raw_out ? raw_out + b0 : nullptr,
+                               status_out ? status_out + b0 : nullptr, s)) != LK_OK)
+            return st;
+        blk.resize((size_t)m);
+        bst.resize((size_t)m);
+        LK_CUDA(ctx, cudaMemcpyAsync(blk.data(), ctx->ws.lk.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LK_CUDA(ctx, cudaMemcpyAsync(bst.data(), ctx->ws.status.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LK_CUDA(ctx, cudaStreamSynchronize(s));
+        *n_checked = b1;
+        for (int64_t k = 0; k < m; ++k) {
+            if (bst[(size_t)k] != LK_OK || blk[(size_t)k] != he[(size_t)(b0 + k)]) {
+                *first_mismatch = b0 + k;
+                return LK_OK;
+            }
+        }
+        b0 = b1;
+    }
+    return LK_OK;
+}

@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "LK_OK", 1: "LK_ERR_ARG", 2: "LK_ERR_ZERO_SEGMENT", 3: "LK_ER
 
 EXPORTED = ["lk_default_options", "lk_create", "lk_update", "lk_verify", "lk_sync", "lk_get_stats",
             "lk_destroy", "lk_last_error", "lk_plan_create", "lk_plan_run", "lk_plan_destroy",
-            "lk_verify_noalloc", "lk_autotune", "lk_tune_get", "lk_tune_set", "lk_server_default_options", "lk_server_create", "lk_server_stream",
+            "lk_verify_noalloc", "lk_verify_expected", "lk_autotune", "lk_tune_get", "lk_tune_set", "lk_server_default_options", "lk_server_create", "lk_server_stream",
             "lk_server_submit", "lk_server_step", "lk_server_poll", "lk_server_get_stats",
             "lk_server_last_error", "lk_server_destroy"]
 
@@ -132,6 +132,9 @@ def load(path: str | None = None):
     lib.lk_server_last_error.argtypes = [vp]
     lib.lk_server_destroy.restype = None
     lib.lk_server_destroy.argtypes = [vp]
+    lib.lk_verify_expected.restype = ctypes.c_int
+    lib.lk_verify_expected.argtypes = [vp, i32p, vp, i64, i64, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64), vp, vp, vp, vp]
     lib.lk_autotune.restype = ctypes.c_int
     lib.lk_autotune.argtypes = [vp, i32p, i64, vp]
     lib.lk_tune_get.restype = ctypes.c_int
@@ -273,6 +276,18 @@ def lk_verify_noalloc(vertices, loop_offsets, loop_pairs, lk_out=None, raw_out=N
                                     _ptr(loop_offsets), int(loop_offsets.shape[0]) - 1, _ptr(loop_pairs),
                                     int(loop_pairs.shape[0]), _ptr(lk_out), _ptr(raw_out), _ptr(status_out),
                                     _stream(stream)))
+
+
+def lk_verify_expected(ctx, loop_pairs, expected, batch_segment_pairs=0, lk_out=None, raw_out=None,
+                       status_out=None, stream=None):
+    """Returns (first_mismatch or -1, pairs checked)."""
+    if str(loop_pairs.dtype).split(".")[-1] != "int32" or str(expected.dtype).split(".")[-1] != "int32":
+        raise TypeError("loop_pairs and expected must be int32")
+    fm, nc = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().lk_verify_expected(ctx, _ptr(loop_pairs), _ptr(expected), int(loop_pairs.shape[0]),
+                                     int(batch_segment_pairs), ctypes.byref(fm), ctypes.byref(nc), _ptr(lk_out),
+                                     _ptr(raw_out), _ptr(status_out), _stream(stream)), ctx)
+    return fm.value, nc.value
 
 
 def lk_autotune(ctx, loop_pairs, stream=None):

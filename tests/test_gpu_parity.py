@@ -331,3 +331,25 @@ def test_autotune_changes_only_the_split(tmp_path):
         assert np.max(np.abs(forced[1] - base[1])) <= 1e-9
     finally:
         lk.lk_destroy(ctx)
+
+
+def test_early_exit_stops_at_the_first_changed_link():
+    g = W.chainmail(rows=10, cols=20)
+    n = g.pairs.shape[0]
+    ctx = lk.lk_create(g.vertices, g.offsets)
+    try:
+        cert = np.zeros(n, np.int32)
+        lk.lk_verify(ctx, g.pairs, cert)
+        fm, checked = lk.lk_verify_expected(ctx, g.pairs, cert, 1 << 22)
+        assert fm == -1 and checked == n
+        k = (2 * n) // 3
+        bad = cert.copy()
+        bad[k] += 1                                   # a "pull-through" at pair k
+        out = np.full(n, 77, np.int32)
+        fm, checked = lk.lk_verify_expected(ctx, g.pairs, bad, 1 << 22, out)
+        assert fm == k and k < checked < n            # stopped after the batch holding k
+        assert np.array_equal(out[:checked], cert[:checked]) and np.all(out[checked:] == 77)
+        dev = torch.from_numpy(bad).cuda()
+        assert lk.lk_verify_expected(ctx, torch.from_numpy(g.pairs).cuda(), dev, 0)[0] == k
+    finally:
+        lk.lk_destroy(ctx)
