@@ -37,7 +37,14 @@ UNIT = "segment-pair evals/s"
 FLOPS_PER_SP = 58.0
 # FP32 peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-KERNELS_PER_STEP = 5  # pair_frames, sweep_mixed, sweep_careful, near_fix, reduce
+# Kernels one chainmail step launches: pair_frames, sweep_packed (fast variant;
+# the accurate launch has no items), careful_chunk x2, sweep_careful x2,
+# near_fix, reduce.
+KERNELS_PER_STEP = 8
+# DRAM bytes (read + write) of one sweep_packed_kernel<fast> launch on this
+# workload, from one ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum); set to None whenever the kernel changes.
+SWEEP_TRAFFIC_BYTES = 18112512
 
 
 def parse():
@@ -348,7 +355,8 @@ def run_ours(args):
                           "max_abs_raw_diff_vs_mixed": float(np.max(np.abs(raw64_host - raw_host)))},
         "fp64_recomputed_segment_pairs": stats["fp64_pairs"], "careful_items": stats["careful_items"], "careful_chunks": stats["careful_chunks"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "sweep_mixed_kernel",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": SWEEP_TRAFFIC_BYTES,
+                     "traffic_unit": "bytes per launch", "kernel": "sweep_packed_kernel<fast>",
                      "kernel_ms": sweep_avg, "flops_per_segment_pair": FLOPS_PER_SP,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
