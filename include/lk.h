@@ -79,8 +79,11 @@ typedef struct lk_options {
     int64_t accurate_threshold; /* LK_MIXED: loop pairs with at least this many segment pairs use
                             the bias-free FP32 arithmetic (refined sqrt and division, shifted
                             denominators); smaller pairs use the hardware approximations,
-                            whose relative bias (~5e-9) is negligible for them.  0 = always
-                            accurate; default 1<<22 */
+                            whose relative bias (~5e-9) is negligible for them, and sum a
+                            cell column's terms over a 32-row chunk by angle summation
+                            (Appendix B: one arctangent per column and chunk); a chunk whose
+                            nearest corner is within 4.5 segment lengths is swept per pair
+                            instead.  0 = always accurate; default 1<<22 */
 } lk_options;
 
 typedef struct lk_stats {
@@ -114,7 +117,10 @@ void lk_default_options(lk_options* opt);
  * non-finite coordinates), LK_ERR_ZERO_SEGMENT (a segment of length < eps*xi,
  * xi the mean absolute coordinate and eps the machine epsilon of vdtype:
  * Algorithm 3's input check), LK_ERR_OOM, LK_ERR_CUDA.  On error *out is NULL.
- * The call returns after the geometry is on the device.
+ * The call returns after the geometry is on the device.  Device memory: 48
+ * bytes per vertex (FP64 coordinates plus an FP32 copy relative to each
+ * loop's box centre, which the mixed-precision sweep reads) and 48 bytes per
+ * loop (its box).
  */
 lk_status lk_create(lk_ctx** out, const void* vertices, lk_dtype vdtype, int64_t n_vertices,
                     const int64_t* loop_offsets, int64_t n_loops, const lk_options* opt,

@@ -133,6 +133,7 @@ struct lk_ctx {
     int64_t n_loops = 0;
     std::vector<int64_t> h_offsets;
     Vtx* d_V = nullptr;
+    float4* d_R = nullptr;    // FP32 loop-relative copy of d_V (the mixed path reads it)
     int64_t* d_offsets = nullptr;
     double* d_aabb = nullptr;
     void* d_stage = nullptr;  // staging for host-side lk_update data
@@ -226,6 +227,7 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
         const int64_t nb = ctx->h_offsets[b + 1] - ctx->h_offsets[b];
         const bool a_rows = na >= nb;
         t.V = ctx->d_V;
+        t.R = ctx->d_R;
         t.row_loop = a_rows ? a : b;
         t.col_loop = a_rows ? b : a;
         t.row_base = ctx->h_offsets[t.row_loop];
@@ -243,7 +245,7 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
         items[(size_t)p] = (int64_t)t.col_tiles * row_tiles;
         cost[(size_t)p] = (double)std::min(t.tile_rows, t.n_rows) * std::min(tile_cols, t.n_cols);
         t.status = LK_OK;
-        t.scale = 1.0;
+        t.scale = 1.0f;
         t.accurate = (int64_t)t.n_rows * t.n_cols >= ctx->opt.accurate_threshold ? 1 : 0;
         pk.segment_pairs += (int64_t)t.n_rows * t.n_cols;
         pk.tile_rows_max = std::max(pk.tile_rows_max, t.tile_rows);
@@ -592,10 +594,11 @@ lk_status lk_create(lk_ctx** out, const void* vertices, lk_dtype vdtype, int64_t
     cudaError_t e = cudaMalloc(&ctx->d_V, (size_t)n_vertices * sizeof(Vtx));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_offsets, off.size() * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_aabb, (size_t)n_loops * 6 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_R, (size_t)n_vertices * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_V, hv.data(), hv.size() * sizeof(Vtx), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_offsets, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
-        lk::launch_loop_aabb(ctx->d_V, ctx->d_offsets, n_loops, ctx->d_aabb, s);
+        lk::launch_loop_aabb(ctx->d_V, ctx->d_offsets, n_loops, ctx->d_aabb, ctx->d_R, s);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -627,7 +630,7 @@ lk_status lk_update(lk_ctx* ctx, const void* data, lk_dtype dtype, int is_delta,
         src = ctx->d_stage;
     }
     lk::launch_update(ctx->d_V, src, dtype == LK_F32 ? 0 : 1, is_delta ? 1 : 0, ctx->n_vertices, s);
-    lk::launch_loop_aabb(ctx->d_V, ctx->d_offsets, ctx->n_loops, ctx->d_aabb, s);
+    lk::launch_loop_aabb(ctx->d_V, ctx->d_offsets, ctx->n_loops, ctx->d_aabb, ctx->d_R, s);
     LK_CUDA(ctx, cudaGetLastError());
     return LK_OK;
 }
@@ -691,6 +694,7 @@ void lk_destroy(lk_ctx* ctx) {
     if (ctx->d_V) cudaFree(ctx->d_V);
     if (ctx->d_offsets) cudaFree(ctx->d_offsets);
     if (ctx->d_aabb) cudaFree(ctx->d_aabb);
+    if (ctx->d_R) cudaFree(ctx->d_R);
     if (ctx->d_stage) cudaFree(ctx->d_stage);
     delete ctx;
 }
@@ -873,6 +877,7 @@ extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, in
 
     NoallocLayout L(scratch);
     ctx.d_V = L.take<Vtx>((size_t)kNoallocMaxVertices);
+    ctx.d_R = L.take<float4>((size_t)kNoallocMaxVertices);
     double* raw_in = L.take<double>((size_t)kNoallocMaxVertices * 3);   // host vertices staged here
     ctx.d_offsets = L.take<int64_t>((size_t)kNoallocMaxLoops + 1);
     ctx.d_aabb = L.take<double>((size_t)kNoallocMaxLoops * 6);
@@ -920,7 +925,7 @@ extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, in
                                     cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "lk_verify_noalloc: offsets");
     lk::launch_update(ctx.d_V, vsrc, vdtype == LK_F32 ? 0 : 1, 0, n_vertices, s);
-    lk::launch_loop_aabb(ctx.d_V, ctx.d_offsets, n_loops, ctx.d_aabb, s);
+    lk::launch_loop_aabb(ctx.d_V, ctx.d_offsets, n_loops, ctx.d_aabb, ctx.d_R, s);
     if ((st = ensure_workspace(&ctx, ws, n_pairs, pk.n_items, pk.n_chunks)) != LK_OK ||
         (st = upload_packed(&ctx, ws, pk, s)) != LK_OK || (st = enqueue_verify(&ctx, ws, pk, s)) != LK_OK ||
         (st = copy_outputs(&ctx, ws, n_pairs, lk_out, raw_out, status_out, s)) != LK_OK)

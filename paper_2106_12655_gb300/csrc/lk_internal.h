@@ -38,8 +38,21 @@ constexpr double kChunkFixScale = 4294967296.0;  // 2^32
 constexpr int kFlagIntersect = 1;
 
 // One loop pair of a verify call, laid out for the device.
+//
+// The mixed path reads an FP32 copy of the geometry, R[v] = (float)(v -
+// centre of v's loop box), refreshed with the boxes whenever the FP64
+// vertices change.  The pair's frame has its origin at the centre of the union of the two loop
+// boxes and a power-of-two scale that maps the union into [-1, 1]^3.  Every
+// kernel of the mixed path sees a vertex of the pair as the FP32 value
+//     fmaf(R[v], scale, off)   (per coordinate)
+// with off = (float)((loop centre - origin) * scale) of the vertex's loop.
+// Because the scale is a power of two, R[v] * scale is exact and this is the
+// single rounding of (R[v] + loop centre - origin) * scale; the FP32 sweep and
+// the FP64 recompute both use these values, so a pair's sum is the linking
+// integral of one closed polyline pair.
 struct PairTask {
-    const Vtx* V;        // the geometry this pair's loops live in
+    const Vtx* V;        // FP64 geometry (read by the all-FP64 path)
+    const float4* R;     // FP32 loop-relative geometry (read by the mixed path)
     int64_t row_base;    // first vertex of the row loop (segments j, iterated)
     int64_t col_base;    // first vertex of the column loop (segments i, across lanes)
     int32_t n_rows;      // segments (= vertices) of the row loop
@@ -52,8 +65,10 @@ struct PairTask {
     int32_t status;      // LK_OK, or LK_ERR_ARG for an invalid pair (then it has no items)
     int32_t accurate;    // 1: bias-free FP32 arithmetic variant (large pairs)
     int32_t pad;
-    double origin[3];    // staged vertex = (float)((v - origin) * scale)
-    double scale;
+    float row_off[4];    // frame offset of the row loop's vertices ([3] unused)
+    float col_off[4];    // frame offset of the column loop's vertices ([3] unused)
+    float scale;         // power of two
+    float pad2[3];
 };
 
 // A segment pair queued for FP64 recompute.
@@ -121,7 +136,7 @@ struct ReduceArgs {
 
 // Kernel launchers (lk_kernels.cu).
 void launch_loop_aabb(const Vtx* V, const int64_t* offsets, int64_t n_loops, double* aabb,
-                      cudaStream_t s);
+                      float4* R, cudaStream_t s);
 void launch_pair_frames(PairTask* tasks, int64_t n_tasks, const double* aabb, cudaStream_t s);
 void launch_sweep_mixed(const SweepArgs& a, bool accurate, int64_t item_lo, int64_t item_hi,
                         unsigned long long* counter, int grid, cudaStream_t s);

@@ -218,14 +218,49 @@ def test_near_segments_take_the_fp64_path():
     assert abs(raw[0] - ref[0]) <= RAW_TOL
     assert s["fp64_pairs"] > 0
     assert s["careful_chunks"] > 0 and s["careful_items"] == 0
-    # a one-entry chunk list hands whole items to the careful pass instead
+    # a one-entry chunk list hands whole items to the careful pass instead;
+    # that pass sums every segment pair's arctangent, the bulk sweep sums its
+    # chunks by angle summation, so the two agree to FP32 rounding of the sums
     lk3, raw3, st3, s3 = run(g, stats=True, chunk_capacity=1)
     assert s3["careful_items"] > 0
-    assert st3[0] == 0 and lk3[0] == lk_o[0] and abs(raw3[0] - raw[0]) <= 1e-9
+    assert st3[0] == 0 and lk3[0] == lk_o[0] and abs(raw3[0] - raw[0]) <= 1e-8
+    assert abs(raw3[0] - ref[0]) <= RAW_TOL
     # a tiny list forces the in-place FP64 evaluation of the overflow
     lk2, raw2, st2, s2 = run(g, stats=True, near_capacity=3)
     assert s2["near_overflow"] > 0
     assert st2[0] == 0 and lk2[0] == lk_o[0] and abs(raw2[0] - ref[0]) <= RAW_TOL
+
+
+def threaded_ring(n_small, n_big, centre_row=16, r_small=0.1, seed=7):
+    """A unit ring (n_big segments) threaded by a ring of radius r_small centred
+    on its wire next to row segment centre_row, in the plane normal to the
+    wire: linked (lambda = -1), every vertex-vertex distance about r_small, the
+    small ring's segments 2*pi*r_small/n_small long."""
+    rng = np.random.default_rng(seed)
+    t = 2 * np.pi * np.arange(n_big) / n_big
+    big = np.stack([np.cos(t), np.sin(t), np.zeros_like(t)], 1)
+    phi = 2 * np.pi * (centre_row + 0.5) / n_big
+    radial, up = np.array([np.cos(phi), np.sin(phi), 0.0]), np.array([0.0, 0.0, 1.0])
+    u = 2 * np.pi * (np.arange(n_small) + 0.5) / n_small
+    small = radial + r_small * (np.cos(u)[:, None] * radial + np.sin(u)[:, None] * up)
+    big += rng.normal(scale=1e-4, size=big.shape)
+    return W.from_loops([big, small], dtype=np.float64, pairs=[[0, 1]])
+
+
+@pytest.mark.parametrize("n_small,n_big,bulk", [(29, 314, True), (48, 512, True), (24, 400, False)])
+def test_angle_summation_large_chunk_angles(n_small, n_big, bulk):
+    """Fast variant.  (29, 314): nearest corners at 4.6 segment lengths, every
+    column of the first chunk turns by about 0.2 rad, so the chunk angle is
+    taken by atan2f; (48, 512): 7.6 lengths, mostly the polynomial; (24, 400):
+    3.8 lengths, closer than the angle-summation bound, so the chunk goes to
+    the per-pair careful pass.  All must match the oracle, and no segment pair
+    is near (m >= 3L), so nothing is recomputed in FP64."""
+    g = threaded_ring(n_small, n_big)
+    raw, ref = check_against_oracle(g)
+    assert ref[0] == pytest.approx(-1.0, abs=1e-9)
+    _, _, _, s = run(g, stats=True)
+    assert s["fp64_pairs"] == 0
+    assert (s["careful_chunks"] == 0) == bulk
 
 
 def test_intersecting_loops_are_reported():
