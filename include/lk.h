@@ -79,7 +79,7 @@ typedef struct lk_options {
     int64_t accurate_threshold; /* LK_MIXED: loop pairs with at least this many segment pairs use
                             the bias-free FP32 arithmetic (refined sqrt and division, shifted
                             denominators); smaller pairs use the hardware approximations,
-                            whose relative bias (~5e-9) is negligible for them, and sum a
+                            whose relative bias (~5e-9) is negligible for them.  Both sum a
                             cell column's terms over a 32-row chunk by angle summation
                             (Appendix B: one arctangent per column and chunk); a chunk whose
                             nearest corner is within 4.5 segment lengths is swept per pair
