@@ -150,6 +150,12 @@ lk_status lk_update(lk_ctx* ctx, const void* data, lk_dtype dtype, int is_delta,
  * call returns with the results written; otherwise it returns after enqueueing
  * and the results are valid once cuda_stream has reached the call's end
  * (lk_sync).  n_pairs = 0 is allowed and does nothing.
+ * Repeated lists: the work decomposition depends only on the pair list, the
+ * loop sizes and the tune table.  When a call passes the same list as the
+ * previous call on this context, the context builds (once) and then replays
+ * a graph plan of it, as lk_plan_create/lk_plan_run would, skipping the host
+ * packing and table uploads; every kernel still runs on the current geometry.
+ * A different list, lk_autotune or lk_tune_set drops that plan.
  * Errors: LK_ERR_ARG, LK_ERR_OOM (mem_budget exceeded or allocation failed),
  * LK_ERR_CUDA.
  */

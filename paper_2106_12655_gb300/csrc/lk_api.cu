@@ -148,6 +148,12 @@ struct lk_ctx {
     cudaEvent_t stats_ev0 = nullptr, stats_ev1 = nullptr;
     cudaStream_t stats_stream = nullptr;
     std::map<uint32_t, int> tune;   // size class -> tile rows chosen by lk_autotune
+    // Repeated pair lists: lk_verify keeps the last list it packed and, when
+    // the same list comes again, a graph plan of it (the packing depends only
+    // on the list, the loop sizes and the tune table, none of which lk_update
+    // changes); the kernels still run in full on the current geometry.
+    std::vector<int32_t> last_pairs;
+    lk_plan* repeat_plan = nullptr;
     std::string err;
 };
 
@@ -159,6 +165,14 @@ struct lk_plan {
     cudaGraphExec_t exec = nullptr;
     cudaStream_t capture = nullptr;
 };
+
+// Forget lk_verify's repeated-list state (the tune table changed, another
+// list came, or the context goes away).
+static void drop_repeat_plan(lk_ctx* ctx) {
+    if (ctx->repeat_plan) lk_plan_destroy(ctx->repeat_plan);
+    ctx->repeat_plan = nullptr;
+    ctx->last_pairs.clear();
+}
 
 namespace {
 
@@ -645,12 +659,23 @@ lk_status lk_verify(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, int
     std::vector<int32_t> hp;
     lk_status st = get_pairs_on_host(ctx, loop_pairs, n_pairs, s, hp);
     if (st != LK_OK) return st;
+    if (hp == ctx->last_pairs) {
+        // the same list as the last call: replay its plan (built on the first repeat)
+        if (!ctx->repeat_plan) {
+            lk_plan* plan = nullptr;
+            if ((st = lk_plan_create(ctx, hp.data(), n_pairs, &plan, cuda_stream)) != LK_OK) return st;
+            ctx->repeat_plan = plan;
+        }
+        return lk_plan_run(ctx->repeat_plan, lk_out, raw_out, status_out, cuda_stream);
+    }
+    drop_repeat_plan(ctx);
     Packed pk;
     if ((st = pack_pairs(ctx, hp.data(), n_pairs, pk)) != LK_OK) return st;
     if ((st = ensure_workspace(ctx, ctx->ws, n_pairs, pk.n_items, pk.n_chunks)) != LK_OK) return st;
     if ((st = upload_packed(ctx, ctx->ws, pk, s)) != LK_OK) return st;
     if ((st = enqueue_verify(ctx, ctx->ws, pk, s)) != LK_OK) return st;
     note_stats(ctx, ctx->ws, pk, s);
+    ctx->last_pairs.swap(hp);
     return copy_outputs(ctx, ctx->ws, n_pairs, lk_out, raw_out, status_out, s);
 }
 
@@ -690,6 +715,7 @@ lk_status lk_get_stats(lk_ctx* ctx, lk_stats* out) {
 
 void lk_destroy(lk_ctx* ctx) {
     if (!ctx) return;
+    drop_repeat_plan(ctx);
     ctx->ws.release();
     if (ctx->d_V) cudaFree(ctx->d_V);
     if (ctx->d_offsets) cudaFree(ctx->d_offsets);
@@ -1540,6 +1566,7 @@ lk_status lk_autotune(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, v
         if (st != LK_OK) break;
         if (best_rows > 0) ctx->tune[kv.first] = best_rows;
     }
+    drop_repeat_plan(ctx);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
@@ -1569,6 +1596,7 @@ lk_status lk_tune_set(lk_ctx* ctx, const int32_t* entries, int64_t n_entries) {
     ctx->tune.clear();
     for (int64_t k = 0; k < n_entries; ++k)
         ctx->tune[((uint32_t)entries[3 * k] << 8) | (uint32_t)entries[3 * k + 1]] = entries[3 * k + 2];
+    drop_repeat_plan(ctx);
     return LK_OK;
 }
 

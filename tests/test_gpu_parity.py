@@ -312,6 +312,38 @@ def test_result_independent_of_batch_and_rerun():
     assert np.array_equal(run(g, g.pairs[shuffled])[1], full[shuffled])
 
 
+def test_repeated_pair_list_replays_a_plan():
+    """lk_verify with the same list again reuses its work tables (a graph plan)
+    and must give, after every lk_update, what a fresh context gives; a
+    different list in between, and a tune-table change, start over."""
+    g = W.ring_chain()
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(5)
+    v = torch.from_numpy(np.ascontiguousarray(g.vertices)).cuda()
+    off = torch.from_numpy(g.offsets).cuda()
+    ctx = lk.lk_create(v, off, None, stream)
+    n = g.pairs.shape[0]
+    other = np.ascontiguousarray(g.pairs[::3])
+    try:
+        for step in range(5):
+            d = rng.normal(scale=2e-3, size=g.vertices.shape)
+            lk.lk_update(ctx, torch.from_numpy(d).cuda(), True, stream)
+            if step == 2:
+                lo2, raw2, st2 = np.zeros(other.shape[0], np.int32), np.zeros(other.shape[0]), np.zeros(other.shape[0], np.int32)
+                lk.lk_verify(ctx, other, lo2, raw2, st2, stream)
+            if step == 3:
+                lk.lk_tune_set(ctx, np.array([[7, 7, 64]], np.int32))
+            lo, raw, st = np.zeros(n, np.int32), np.zeros(n), np.zeros(n, np.int32)
+            lk.lk_verify(ctx, np.ascontiguousarray(g.pairs), lo, raw, st, stream)
+            g = W.Geometry(g.vertices + d, g.offsets, g.pairs, g.name, {})
+            ref_lo, ref_raw, ref_st = run(g)
+            assert np.array_equal(st, ref_st) and np.array_equal(lo, ref_lo)
+            # a changed tune table only regroups the FP64 sums
+            assert np.abs(raw - ref_raw).max() <= (1e-12 if step >= 3 else 0.0)
+    finally:
+        lk.lk_destroy(ctx)
+
+
 def test_update_matches_fresh_context():
     g = W.chainmail(rows=6, cols=10, dtype=np.float32)
     rng = np.random.default_rng(5)
