@@ -162,6 +162,24 @@ lk_status lk_update(lk_ctx* ctx, const void* data, lk_dtype dtype, int is_delta,
 lk_status lk_verify(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, int32_t* lk_out,
                     double* raw_out, int32_t* status_out, void* cuda_stream);
 
+/*
+ * Potential link search (Sec. 3.2, Algorithm 2) on the device: the loop pairs
+ * (i, j), i < j, whose axis-aligned bounding boxes (closed, from the current
+ * resident geometry, i.e. after any lk_update) overlap on all three axes.
+ * Every pair with a nonzero linking number is among them.  The list is sorted
+ * by (i, j) and feeds lk_verify directly.
+ *  pairs_out : [capacity][2] int32, host or device; receives the first
+ *              min(n, capacity) pairs (may be NULL when capacity = 0).
+ *  n_pairs   : receives n, the number of candidate pairs (call with
+ *              capacity 0 to size the output).
+ * Synchronous: returns after the pairs are written.  Device memory: 60 bytes
+ * per loop, plus 8 bytes per pair written to a host destination.  The test is
+ * exact (FP64 box bounds) and costs L(L-1)/2 box tests for L loops.
+ * Errors: LK_ERR_ARG, LK_ERR_OOM, LK_ERR_CUDA.
+ */
+lk_status lk_candidates(lk_ctx* ctx, int32_t* pairs_out, int64_t capacity, int64_t* n_pairs,
+                        void* cuda_stream);
+
 /* Wait until all work the context enqueued on cuda_stream has finished. */
 lk_status lk_sync(lk_ctx* ctx, void* cuda_stream);
 

@@ -25,6 +25,10 @@
  * Parity: pinned by tests/test_oracle_pins.py (Gauss-Legendre quadrature of
  * Eq. 1 per segment pair, exact integer crossing counts, closed forms,
  * invariants, integrality of the polyline sum, midpoint convergence of Eq. 2).
+ * The potential link search (lko_candidates) is pinned by
+ * tests/test_oracle_pls.py (linked pairs are candidates, touching and
+ * one-ulp-separated boxes on each axis, an independent sweep-and-prune,
+ * permutation covariance).
  */
 #include <math.h>
 #include <stdint.h>
@@ -175,6 +179,51 @@ int lko_link_pairs(const double* v, const int64_t* offsets, int64_t nloops, cons
         }
         raw[p] = acc_value(&acc);
     }
+    return 0;
+}
+
+/* Potential link search (Sec. 3.2, Algorithm 2) as its plain definition: the
+ * pairs (i, j), i < j, of loops whose axis-aligned bounding boxes overlap.
+ * A loop's box is the componentwise min and max of its vertices; two closed
+ * boxes overlap when, on each of the three axes, each box's low end is at
+ * most the other's high end.  Pairs are listed in (i, j) order; the first
+ * min(n, capacity) are written to pairs_out and n is returned in *n_out. */
+int lko_candidates(const double* v, const int64_t* offsets, int64_t nloops, int32_t* pairs_out,
+                   int64_t capacity, int64_t* n_out) {
+    if (!v || !offsets || !n_out || nloops < 0 || capacity < 0 || (capacity > 0 && !pairs_out)) return 1;
+    double* box = (double*)malloc((size_t)(nloops > 0 ? nloops : 1) * 6 * sizeof(double));
+    if (!box) return 2;
+    for (int64_t l = 0; l < nloops; ++l) {
+        double* lo = box + 6 * l;
+        double* hi = lo + 3;
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = INFINITY;
+            hi[a] = -INFINITY;
+        }
+        for (int64_t q = offsets[l]; q < offsets[l + 1]; ++q)
+            for (int a = 0; a < 3; ++a) {
+                if (v[3 * q + a] < lo[a]) lo[a] = v[3 * q + a];
+                if (v[3 * q + a] > hi[a]) hi[a] = v[3 * q + a];
+            }
+    }
+    int64_t n = 0;
+    for (int64_t i = 0; i < nloops; ++i) {
+        for (int64_t j = i + 1; j < nloops; ++j) {
+            const double* bi = box + 6 * i;
+            const double* bj = box + 6 * j;
+            int overlap = 1;
+            for (int a = 0; a < 3; ++a)
+                if (!(bi[a] <= bj[3 + a] && bj[a] <= bi[3 + a])) overlap = 0;
+            if (!overlap) continue;
+            if (n < capacity) {
+                pairs_out[2 * n] = (int32_t)i;
+                pairs_out[2 * n + 1] = (int32_t)j;
+            }
+            ++n;
+        }
+    }
+    free(box);
+    *n_out = n;
     return 0;
 }
 

@@ -3,7 +3,8 @@
 Thin ctypes wrapper over ``lk_oracle.c``: a plain FP64 CPU direct summation of
 the Gauss linking number of closed polylines, evaluating the closed-form
 segment-pair term of Eq. 4 (Qu & James 2021, Sec. 2.1) as written, summed over
-every segment pair (Eq. 3; Sec. 3.4.2, Algorithm 5).
+every segment pair (Eq. 3; Sec. 3.4.2, Algorithm 5), and the potential link
+search of Sec. 3.2 (Algorithm 2) as its plain all-pairs box-overlap definition.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s ``cpu_baseline``
 and ``--impl reference`` legs may import this module.  The CUDA library never
@@ -57,6 +58,8 @@ def _bind(lib):
     lib.lko_link_rows.argtypes = [dp, i64, dp, i64, i64p, i64, ctypes.c_int, dp]
     lib.lko_link_pairs.restype = ctypes.c_int
     lib.lko_link_pairs.argtypes = [dp, i64p, i64, i32p, i64, ctypes.c_int, dp]
+    lib.lko_candidates.restype = ctypes.c_int
+    lib.lko_candidates.argtypes = [dp, i64p, i64, i32p, i64, i64p]
     lib.lko_max_threads.restype = ctypes.c_int
     lib.lko_max_threads.argtypes = []
     return lib
@@ -171,3 +174,24 @@ def round_lk(raw) -> np.ndarray:
     """Nearest integer, halves away from zero (the rounding reading used throughout)."""
     raw = np.asarray(raw, dtype=np.float64)
     return (np.sign(raw) * np.floor(np.abs(raw) + 0.5)).astype(np.int64)
+
+
+def candidates(vertices, offsets, lib=None) -> np.ndarray:
+    """Potential link search (Sec. 3.2, Algorithm 2) as its plain definition:
+    int32 [n, 2] pairs (i, j), i < j, in (i, j) order, of loops whose closed
+    axis-aligned bounding boxes overlap on all three axes."""
+    lib = lib or _load()
+    v = _f64(vertices)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    nloops = off.shape[0] - 1
+    n = ctypes.c_int64(0)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    offp = off.ctypes.data_as(i64p)
+    if lib.lko_candidates(_dp(v), offp, nloops, None, 0, ctypes.byref(n)):
+        raise ValueError("oracle: invalid arguments")
+    out = np.zeros((int(n.value), 2), np.int32)
+    if out.shape[0]:
+        if lib.lko_candidates(_dp(v), offp, nloops, out.ctypes.data_as(i32p), out.shape[0], ctypes.byref(n)):
+            raise ValueError("oracle: invalid arguments")
+    return out

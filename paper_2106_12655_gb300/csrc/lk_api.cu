@@ -154,6 +154,12 @@ struct lk_ctx {
     // changes); the kernels still run in full on the current geometry.
     std::vector<int32_t> last_pairs;
     lk_plan* repeat_plan = nullptr;
+    // Potential link search buffers (allocated on first use).
+    long long* d_pls_keys = nullptr;     // [6][n_loops]
+    int32_t* d_pls_counts = nullptr;     // [n_loops]
+    int64_t* d_pls_offsets = nullptr;    // [n_loops]
+    int32_t* d_pls_pairs = nullptr;      // staging for host destinations
+    int64_t pls_pairs_cap = 0;
     std::string err;
 };
 
@@ -679,6 +685,65 @@ lk_status lk_verify(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, int
     return copy_outputs(ctx, ctx->ws, n_pairs, lk_out, raw_out, status_out, s);
 }
 
+lk_status lk_candidates(lk_ctx* ctx, int32_t* pairs_out, int64_t capacity, int64_t* n_pairs,
+                        void* cuda_stream) {
+    if (!ctx) return fail(nullptr, LK_ERR_ARG, "lk_candidates: NULL context");
+    if (!n_pairs || capacity < 0 || (capacity > 0 && !pairs_out))
+        return fail(ctx, LK_ERR_ARG, "lk_candidates: invalid output arguments");
+    *n_pairs = 0;
+    const int64_t L = ctx->n_loops;
+    if (L < 2) return LK_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!ctx->d_pls_keys) {
+        cudaError_t e = cudaMalloc(&ctx->d_pls_keys, (size_t)L * 6 * sizeof(long long));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_pls_counts, (size_t)L * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_pls_offsets, (size_t)L * sizeof(int64_t));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, LK_ERR_OOM, "lk_candidates: device allocation failed");
+        }
+    }
+    lk::launch_pls_keys(ctx->d_aabb, L, ctx->d_pls_keys, s);
+    lk::launch_pls_count(ctx->d_pls_keys, L, ctx->d_pls_counts, s);
+    std::vector<int32_t> counts((size_t)L);
+    LK_CUDA(ctx, cudaMemcpyAsync(counts.data(), ctx->d_pls_counts, (size_t)L * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, s));
+    LK_CUDA(ctx, cudaStreamSynchronize(s));
+    std::vector<int64_t> offsets((size_t)L);
+    int64_t total = 0;
+    for (int64_t i = 0; i < L; ++i) {
+        offsets[(size_t)i] = total;
+        total += counts[(size_t)i];
+    }
+    const int64_t m = std::min(total, capacity);
+    if (m > 0) {
+        int32_t* dst = pairs_out;
+        const bool host = !is_device_ptr(pairs_out);
+        if (host) {
+            if (ctx->pls_pairs_cap < m) {
+                if (ctx->d_pls_pairs) cudaFree(ctx->d_pls_pairs);
+                ctx->d_pls_pairs = nullptr;
+                ctx->pls_pairs_cap = 0;
+                if (cudaMalloc(&ctx->d_pls_pairs, (size_t)m * 2 * sizeof(int32_t)) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(ctx, LK_ERR_OOM, "lk_candidates: device allocation failed");
+                }
+                ctx->pls_pairs_cap = m;
+            }
+            dst = ctx->d_pls_pairs;
+        }
+        LK_CUDA(ctx, cudaMemcpyAsync(ctx->d_pls_offsets, offsets.data(), (size_t)L * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, s));
+        lk::launch_pls_write(ctx->d_pls_keys, L, ctx->d_pls_offsets, dst, m, s);
+        LK_CUDA(ctx, cudaGetLastError());
+        if (host)
+            LK_CUDA(ctx, cudaMemcpyAsync(pairs_out, dst, (size_t)m * 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LK_CUDA(ctx, cudaStreamSynchronize(s));
+    }
+    *n_pairs = total;
+    return LK_OK;
+}
+
 lk_status lk_sync(lk_ctx* ctx, void* cuda_stream) {
     if (!ctx) return fail(nullptr, LK_ERR_ARG, "lk_sync: NULL context");
     LK_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)cuda_stream));
@@ -721,6 +786,10 @@ void lk_destroy(lk_ctx* ctx) {
     if (ctx->d_offsets) cudaFree(ctx->d_offsets);
     if (ctx->d_aabb) cudaFree(ctx->d_aabb);
     if (ctx->d_R) cudaFree(ctx->d_R);
+    if (ctx->d_pls_keys) cudaFree(ctx->d_pls_keys);
+    if (ctx->d_pls_counts) cudaFree(ctx->d_pls_counts);
+    if (ctx->d_pls_offsets) cudaFree(ctx->d_pls_offsets);
+    if (ctx->d_pls_pairs) cudaFree(ctx->d_pls_pairs);
     if (ctx->d_stage) cudaFree(ctx->d_stage);
     delete ctx;
 }

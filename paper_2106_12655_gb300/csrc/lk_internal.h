@@ -151,6 +151,12 @@ int wave_blocks_per_sm(bool accurate);
 void launch_reduce(const ReduceArgs& a, cudaStream_t s);
 void launch_update(Vtx* V, const void* data, int dtype, int is_delta, int64_t n, cudaStream_t s);
 int sweep_mixed_blocks_per_sm(bool accurate);
+
+// Potential link search (lk_pls.cu).
+void launch_pls_keys(const double* aabb, int64_t n_loops, long long* keys, cudaStream_t s);
+void launch_pls_count(const long long* keys, int64_t n_loops, int32_t* counts, cudaStream_t s);
+void launch_pls_write(const long long* keys, int64_t n_loops, const int64_t* offsets, int32_t* pairs,
+                      int64_t capacity, cudaStream_t s);
 int sweep_f64_blocks_per_sm();
 int sweep_careful_blocks_per_sm();
 

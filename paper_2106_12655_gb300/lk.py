@@ -102,6 +102,8 @@ def load(path: str | None = None):
     lib.lk_verify.argtypes = [vp, i32p, i64, vp, vp, vp, vp]
     lib.lk_sync.restype = ctypes.c_int
     lib.lk_sync.argtypes = [vp, vp]
+    lib.lk_candidates.restype = ctypes.c_int
+    lib.lk_candidates.argtypes = [vp, vp, i64, ctypes.POINTER(i64), vp]
     lib.lk_get_stats.restype = ctypes.c_int
     lib.lk_get_stats.argtypes = [vp, ctypes.POINTER(lk_stats)]
     lib.lk_destroy.restype = None
@@ -215,6 +217,22 @@ def lk_create(vertices, loop_offsets, options: lk_options | None = None, stream=
 
 def lk_update(ctx, data, is_delta: bool, stream=None):
     _check(load().lk_update(ctx, _ptr(data), _dtype_code(data), 1 if is_delta else 0, _stream(stream)), ctx)
+
+
+def lk_candidates(ctx, pairs_out=None, stream=None):
+    """Potential link search on the device.  With pairs_out (int32 [capacity, 2],
+    host or device) writes the first min(n, capacity) pairs and returns n;
+    without it returns a new int32 numpy array [n, 2] of all candidate pairs."""
+    n = ctypes.c_int64(0)
+    if pairs_out is not None:
+        cap = int(pairs_out.shape[0]) if len(pairs_out.shape) > 0 else 0
+        _check(load().lk_candidates(ctx, _ptr(pairs_out) if cap else None, cap, ctypes.byref(n), _stream(stream)), ctx)
+        return int(n.value)
+    _check(load().lk_candidates(ctx, None, 0, ctypes.byref(n), _stream(stream)), ctx)
+    out = np.zeros((int(n.value), 2), np.int32)
+    if out.shape[0]:
+        _check(load().lk_candidates(ctx, _ptr(out), out.shape[0], ctypes.byref(n), _stream(stream)), ctx)
+    return out
 
 
 def lk_verify(ctx, loop_pairs, lk_out=None, raw_out=None, status_out=None, stream=None):
