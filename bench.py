@@ -160,10 +160,36 @@ def serving_block(args):
                                  "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                                  "n_requests": len(plan), "nonok_pair_status": bad})
         out["server_stats"] = lk.lk_server_get_stats(srv)
+        out["potential_link_search"] = pls_block(scenes)
         return out
     finally:
         lk.lk_server_destroy(srv)
         S.close(scenes)
+
+
+def pls_block(scenes):
+    """Device potential link search (lk_candidates) on each resident pile:
+    wall time of the synchronous call (median of 10) and whether its list
+    equals the pile's candidate list."""
+    import torch
+    from paper_2106_12655_gb300 import lk
+
+    out = []
+    for sc in scenes:
+        n = lk.lk_candidates(sc.ctx, np.zeros((0, 2), np.int32))
+        buf = torch.zeros((max(n, 1), 2), dtype=torch.int32, device="cuda")
+        ts = []
+        for _ in range(12):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lk.lk_candidates(sc.ctx, buf)
+            ts.append(time.perf_counter() - t0)
+        got = buf[:n].cpu().numpy()
+        want = np.ascontiguousarray(sc.geometry.pairs)
+        out.append({"rings": sc.geometry.n_loops, "candidates": n, "ms": 1e3 * statistics.median(ts[2:]),
+                    "box_tests_per_s": sc.geometry.n_loops * (sc.geometry.n_loops - 1) / 2 / statistics.median(ts[2:]),
+                    "equals_pile_pairs": bool(got.shape == want.shape and np.array_equal(got, want))})
+    return out
 
 
 def cpu_baseline(g):
