@@ -271,7 +271,10 @@ typedef struct lk_server_options {
     size_t arena_bytes;   /* device memory for request work buffers (default 1 GiB) */
     size_t host_bytes;    /* pinned host memory for staged item tables and results (default 256 MiB) */
     int64_t wave_items;   /* work items per wave (default 16384) */
-    int near_capacity;    /* FP64 recompute list entries per request (default 4096) */
+    int near_capacity;    /* FP64 recompute list entries per request (default 65536, 1 MB of
+                             arena; a request of chainmail piles with 64-256-segment rings
+                             has ~1.5 near segment pairs per loop pair, and entries beyond
+                             the list are evaluated in place, much more slowly) */
     int max_queue;        /* queued requests before submit returns LK_ERR_BUSY (default 65536) */
 } lk_server_options;
 
@@ -282,6 +285,10 @@ typedef struct lk_server_stats {
     int64_t items_launched;
     int64_t max_requests_per_wave;       /* most requests that shared one wave */
     int64_t arena_used;                  /* bytes of the device arena in use now */
+    int64_t near_overflow;               /* FP64 recomputes that did not fit a request's list
+                                            (evaluated in place, slowly): raise near_capacity */
+    int64_t careful_items;               /* whole items swept again per pair (chunk list full) */
+    int64_t careful_chunks;              /* 32-row chunks swept again per pair */
 } lk_server_stats;
 
 void lk_server_default_options(lk_server_options* opt);
@@ -302,6 +309,11 @@ lk_status lk_server_step(lk_server* srv, int wait);
  * *done = 0 while it is queued or running. */
 lk_status lk_server_poll(lk_server* srv, int64_t ticket, int* done, int32_t* lk_out, double* raw_out,
                          int32_t* status_out);
+/* Tickets of requests that have finished (as seen by lk_server_step) and were
+ * not reported before, in completion order: up to capacity of them are
+ * written to tickets[], *n_done receives how many.  A reported ticket stays
+ * valid for lk_server_poll, which copies its results and releases it. */
+lk_status lk_server_completed(lk_server* srv, int64_t* tickets, int64_t capacity, int64_t* n_done);
 lk_status lk_server_get_stats(lk_server* srv, lk_server_stats* out);
 const char* lk_server_last_error(const lk_server* srv);
 /* Waits for the server's stream, then frees everything it owns. */

@@ -229,79 +229,95 @@ int default_tile_rows(int64_t n_rows, int64_t n_cols, int tile_cols, int user_ro
 lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
     const bool f64 = ctx->opt.precision == LK_ALL_F64;
     const int tile_cols = f64 ? lk::kF64TileCols : lk::kTileCols;
-    pk.tasks.assign((size_t)n, PairTask{});
     pk.tile_cols = tile_cols;
     pk.tile_rows_max = 0;
     pk.segment_pairs = 0;
-    std::vector<int64_t> items((size_t)n, 0);
-    std::vector<double> cost((size_t)n, 0.0);
+    // Per pair: its shape, work items and sort key.  Accurate-variant pairs go
+    // first (they run in their own launch), then within each variant the
+    // largest items first, so that the persistent grid's tail is made of small
+    // ones; ties keep the input order.  key = (variant, clamped item cost),
+    // sorted ascending by a stable LSD radix sort.
+    struct Shape {
+        int32_t row_loop, col_loop, n_rows, n_cols, tile_rows, col_tiles, status, accurate;
+        int64_t items;
+    };
+    std::vector<Shape> sh((size_t)n);
+    std::vector<uint32_t> key((size_t)n);
+    const bool tuned = !f64 && ctx->opt.tile_rows <= 0 && !ctx->tune.empty();
     for (int64_t p = 0; p < n; ++p) {
-        PairTask& t = pk.tasks[(size_t)p];
-        t.out_index = (int32_t)p;
+        Shape& t = sh[(size_t)p];
         const int32_t a = pairs[2 * p], b = pairs[2 * p + 1];
         if (a < 0 || b < 0 || a >= ctx->n_loops || b >= ctx->n_loops || a == b) {
-            t.status = LK_ERR_ARG;
+            t = Shape{0, 0, 0, 0, 0, 0, LK_ERR_ARG, 0, 0};
+            key[(size_t)p] = 0xffffffffu;                       // invalid pairs last (no items)
             continue;
         }
         const int64_t na = ctx->h_offsets[a + 1] - ctx->h_offsets[a];
         const int64_t nb = ctx->h_offsets[b + 1] - ctx->h_offsets[b];
         const bool a_rows = na >= nb;
-        t.V = ctx->d_V;
-        t.R = ctx->d_R;
         t.row_loop = a_rows ? a : b;
         t.col_loop = a_rows ? b : a;
-        t.row_base = ctx->h_offsets[t.row_loop];
-        t.col_base = ctx->h_offsets[t.col_loop];
         t.n_rows = (int32_t)(a_rows ? na : nb);
         t.n_cols = (int32_t)(a_rows ? nb : na);
         int rows = ctx->opt.tile_rows;
-        if (rows <= 0 && !f64) {
+        if (tuned) {
             auto it = ctx->tune.find(size_class(t.n_rows, t.n_cols));
             if (it != ctx->tune.end()) rows = it->second;
         }
         t.tile_rows = default_tile_rows(t.n_rows, t.n_cols, tile_cols, rows);
         t.col_tiles = (t.n_cols + tile_cols - 1) / tile_cols;
-        const int64_t row_tiles = (t.n_rows + t.tile_rows - 1) / t.tile_rows;
-        items[(size_t)p] = (int64_t)t.col_tiles * row_tiles;
-        cost[(size_t)p] = (double)std::min(t.tile_rows, t.n_rows) * std::min(tile_cols, t.n_cols);
+        t.items = (int64_t)t.col_tiles * ((t.n_rows + t.tile_rows - 1) / t.tile_rows);
         t.status = LK_OK;
-        t.scale = 1.0f;
         t.accurate = (int64_t)t.n_rows * t.n_cols >= ctx->opt.accurate_threshold ? 1 : 0;
+        const int64_t cost = (int64_t)std::min(t.tile_rows, t.n_rows) * std::min(tile_cols, t.n_cols);
+        const uint32_t c = (uint32_t)std::min<int64_t>(cost, 0x7ffffffe);
+        key[(size_t)p] = (t.accurate ? 0u : 0x80000000u) | (0x7ffffffeu - c);
         pk.segment_pairs += (int64_t)t.n_rows * t.n_cols;
         pk.tile_rows_max = std::max(pk.tile_rows_max, t.tile_rows);
     }
-    // Accurate-variant pairs first (they run in their own launch), then within
-    // each variant the largest items first, so that the persistent grid's
-    // tail is made of small ones.
-    std::vector<int64_t> order((size_t)n);
+    std::vector<int64_t> order((size_t)n), tmp((size_t)n);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
-        const int ax = pk.tasks[(size_t)x].accurate, ay = pk.tasks[(size_t)y].accurate;
-        if (ax != ay) return ax > ay;
-        return cost[(size_t)x] > cost[(size_t)y];
-    });
-    std::vector<PairTask> sorted((size_t)n);
-    pk.item_begin.assign((size_t)n + 1, 0);
-    for (int64_t k = 0; k < n; ++k) {
-        sorted[(size_t)k] = pk.tasks[(size_t)order[(size_t)k]];
-        pk.item_begin[(size_t)k + 1] = pk.item_begin[(size_t)k] + items[(size_t)order[(size_t)k]];
+    for (int shift = 0; shift < 32; shift += 8) {
+        size_t cnt[257] = {};
+        for (int64_t k = 0; k < n; ++k) ++cnt[((key[(size_t)order[(size_t)k]] >> shift) & 0xffu) + 1];
+        if (cnt[1 + ((key[(size_t)order[0]] >> shift) & 0xffu)] == (size_t)n) continue;   // one digit value
+        for (int d = 0; d < 256; ++d) cnt[d + 1] += cnt[d];
+        for (int64_t k = 0; k < n; ++k) tmp[cnt[(key[(size_t)order[(size_t)k]] >> shift) & 0xffu]++] = order[(size_t)k];
+        order.swap(tmp);
     }
-    pk.tasks.swap(sorted);
-    pk.n_items = pk.item_begin[(size_t)n];
+    pk.tasks.resize((size_t)n);
+    pk.item_begin.assign((size_t)n + 1, 0);
     pk.n_acc_items = 0;
     pk.n_chunks = 0;
     for (int64_t k = 0; k < n; ++k) {
-        const PairTask& t = pk.tasks[(size_t)k];
-        if (t.status != LK_OK) continue;
-        const int64_t row_tiles = (t.n_rows + t.tile_rows - 1) / t.tile_rows;
-        const int64_t full = t.n_rows / t.tile_rows, last = t.n_rows - full * t.tile_rows;
-        const int64_t chunks_per_col = full * ((t.tile_rows + lk::kChunkRows - 1) / lk::kChunkRows) +
-                                       (last > 0 ? (last + lk::kChunkRows - 1) / lk::kChunkRows : 0);
-        (void)row_tiles;
-        pk.n_chunks += chunks_per_col * t.col_tiles;
+        const int64_t p = order[(size_t)k];
+        const Shape& q = sh[(size_t)p];
+        PairTask t{};
+        t.out_index = (int32_t)p;
+        t.status = q.status;
+        t.scale = 1.0f;
+        if (q.status == LK_OK) {
+            t.V = ctx->d_V;
+            t.R = ctx->d_R;
+            t.row_loop = q.row_loop;
+            t.col_loop = q.col_loop;
+            t.row_base = ctx->h_offsets[q.row_loop];
+            t.col_base = ctx->h_offsets[q.col_loop];
+            t.n_rows = q.n_rows;
+            t.n_cols = q.n_cols;
+            t.tile_rows = q.tile_rows;
+            t.col_tiles = q.col_tiles;
+            t.accurate = q.accurate;
+            const int64_t full = q.n_rows / q.tile_rows, last = q.n_rows - full * q.tile_rows;
+            const int64_t chunks_per_col = full * ((q.tile_rows + lk::kChunkRows - 1) / lk::kChunkRows) +
+                                           (last > 0 ? (last + lk::kChunkRows - 1) / lk::kChunkRows : 0);
+            pk.n_chunks += chunks_per_col * q.col_tiles;
+        }
+        pk.tasks[(size_t)k] = t;
+        pk.item_begin[(size_t)k + 1] = pk.item_begin[(size_t)k] + q.items;
+        if (q.accurate) pk.n_acc_items = pk.item_begin[(size_t)k + 1];
     }
-    for (int64_t k = 0; k < n; ++k)
-        if (pk.tasks[(size_t)k].accurate) pk.n_acc_items = pk.item_begin[(size_t)k + 1];
+    pk.n_items = pk.item_begin[(size_t)n];
     if (pk.n_items > (int64_t)INT32_MAX * 16)
         return fail(ctx, LK_ERR_ARG, "lk_verify: too many work items");
     pk.item_task.resize((size_t)pk.n_items);
@@ -1102,6 +1118,7 @@ struct Request {
     int32_t* h_lk = nullptr;   // pinned results
     double* h_raw = nullptr;
     int32_t* h_status = nullptr;
+    unsigned long long* h_counters = nullptr;   // the request's 8 work counters, copied back
     lk::SweepArgs args{};
     int64_t next_item = 0;
     int state = kQueued;
@@ -1147,7 +1164,8 @@ size_t request_layout(const Packed& pk, int near_cap, Workspace* ws, uintptr_t b
 }
 
 size_t request_result_bytes(size_t P) {
-    return ((P * 4 + 255) & ~(size_t)255) + ((P * 8 + 255) & ~(size_t)255) + ((P * 4 + 255) & ~(size_t)255);
+    return ((P * 4 + 255) & ~(size_t)255) + ((P * 8 + 255) & ~(size_t)255) + ((P * 4 + 255) & ~(size_t)255) +
+           256;   // the request's work counters
 }
 
 // Pinned host bytes of a request: its results, then its staged item tables.
@@ -1170,6 +1188,7 @@ struct lk_server {
     std::deque<Request*> queue;
     std::vector<Request*> running;     // admitted, in admission order
     std::map<int64_t, Request*> all;
+    std::deque<int64_t> finished;      // tickets done and not yet reported by lk_server_completed
     std::deque<Wave> waves;
     bool slot_busy[kWaveSlots] = {};
     lk::WaveSeg* h_segs[kWaveSlots] = {};   // pinned staging of each slot's runs
@@ -1235,6 +1254,12 @@ lk_status retire(lk_server* s, bool block) {
         block = false;
         for (Request* r : w.completing) {
             r->state = kDone;
+            s->finished.push_back(r->ticket);
+            // counters: [1] FP64 recomputes evaluated in place, [2] low half the
+            // whole-item hand-overs, [5] low half the chunk hand-overs
+            s->st.near_overflow += (int64_t)r->h_counters[1];
+            s->st.careful_items += (int64_t)(uint32_t)r->h_counters[2];
+            s->st.careful_chunks += (int64_t)(uint32_t)r->h_counters[5];
             s->dev.release(r->dev_off, r->dev_bytes);
             auto it = std::find(s->running.begin(), s->running.end(), r);
             if (it != s->running.end()) s->running.erase(it);
@@ -1271,6 +1296,8 @@ lk_status admit(lk_server* s) {
         r->h_lk = reinterpret_cast<int32_t*>(hb);
         r->h_raw = reinterpret_cast<double*>(hb + ((P * 4 + 255) & ~(size_t)255));
         r->h_status = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(r->h_raw) + ((P * 8 + 255) & ~(size_t)255));
+        r->h_counters = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(r->h_status) +
+                                                              ((P * 4 + 255) & ~(size_t)255));
         r->args = request_args(ctx, r->ws, r->pk, s->opt.near_capacity);
         // Stage the item tables in pinned memory so that their upload is truly
         // asynchronous (a pageable source would make the copy wait for the
@@ -1375,6 +1402,8 @@ lk_status launch_wave(lk_server* s) {
         LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_lk, r->ws.lk.p, P * 4, cudaMemcpyDeviceToHost, st));
         LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_raw, r->ws.raw.p, P * 8, cudaMemcpyDeviceToHost, st));
         LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_status, r->ws.status.p, P * 4, cudaMemcpyDeviceToHost, st));
+        LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_counters, r->ws.counters.p, 8 * sizeof(unsigned long long),
+                                       cudaMemcpyDeviceToHost, st));
     }
     LK_SRV_CUDA(s, cudaGetLastError());
     Wave w;
@@ -1400,7 +1429,7 @@ void lk_server_default_options(lk_server_options* o) {
     o->arena_bytes = (size_t)1 << 30;
     o->host_bytes = (size_t)256 << 20;
     o->wave_items = 16384;
-    o->near_capacity = 4096;
+    o->near_capacity = 1 << 16;
     o->max_queue = 1 << 16;
 }
 
@@ -1487,6 +1516,18 @@ lk_status lk_server_step(lk_server* s, int wait) {
     if ((st = admit(s)) != LK_OK) return st;
     if ((st = launch_wave(s)) != LK_OK) return st;
     if (wait && !s->waves.empty() && (st = retire(s, true)) != LK_OK) return st;
+    return LK_OK;
+}
+
+lk_status lk_server_completed(lk_server* s, int64_t* tickets, int64_t capacity, int64_t* n_done) {
+    if (!s || !n_done || capacity < 0 || (capacity > 0 && !tickets))
+        return srv_fail(s, LK_ERR_ARG, "lk_server_completed: invalid arguments");
+    int64_t k = 0;
+    while (k < capacity && !s->finished.empty()) {
+        tickets[k++] = s->finished.front();
+        s->finished.pop_front();
+    }
+    *n_done = k;
     return LK_OK;
 }
 

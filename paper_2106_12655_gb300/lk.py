@@ -36,8 +36,8 @@ STATUS_NAMES = {0: "LK_OK", 1: "LK_ERR_ARG", 2: "LK_ERR_ZERO_SEGMENT", 3: "LK_ER
 EXPORTED = ["lk_default_options", "lk_create", "lk_update", "lk_verify", "lk_sync", "lk_get_stats",
             "lk_destroy", "lk_last_error", "lk_plan_create", "lk_plan_run", "lk_plan_destroy",
             "lk_verify_noalloc", "lk_verify_expected", "lk_autotune", "lk_tune_get", "lk_tune_set", "lk_server_default_options", "lk_server_create", "lk_server_stream",
-            "lk_server_submit", "lk_server_step", "lk_server_poll", "lk_server_get_stats",
-            "lk_server_last_error", "lk_server_destroy"]
+            "lk_server_submit", "lk_server_step", "lk_server_poll", "lk_server_completed",
+            "lk_server_get_stats", "lk_server_last_error", "lk_server_destroy", "lk_candidates"]
 
 
 class lk_options(ctypes.Structure):
@@ -65,7 +65,8 @@ class lk_server_options(ctypes.Structure):
 class lk_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "queued", "running",
                                                "waves", "waves_in_flight", "items_launched",
-                                               "max_requests_per_wave", "arena_used")]
+                                               "max_requests_per_wave", "arena_used", "near_overflow",
+                                               "careful_items", "careful_chunks")]
 
 
 class LkError(RuntimeError):
@@ -128,6 +129,8 @@ def load(path: str | None = None):
     lib.lk_server_step.argtypes = [vp, ctypes.c_int]
     lib.lk_server_poll.restype = ctypes.c_int
     lib.lk_server_poll.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int), vp, vp, vp]
+    lib.lk_server_completed.restype = ctypes.c_int
+    lib.lk_server_completed.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
     lib.lk_server_get_stats.restype = ctypes.c_int
     lib.lk_server_get_stats.argtypes = [vp, ctypes.POINTER(lk_server_stats)]
     lib.lk_server_last_error.restype = ctypes.c_char_p
@@ -369,6 +372,21 @@ def lk_server_poll(srv, ticket, lk_out=None, raw_out=None, status_out=None) -> b
     _check_srv(load().lk_server_poll(srv, ticket, ctypes.byref(d), _ptr(lk_out), _ptr(raw_out), _ptr(status_out)),
                srv)
     return bool(d.value)
+
+
+_completed_buf = np.zeros(4096, np.int64)
+
+
+def lk_server_completed(srv) -> list:
+    """Tickets finished since the last call, in completion order."""
+    out = []
+    n = ctypes.c_int64(0)
+    while True:
+        _check_srv(load().lk_server_completed(srv, _completed_buf.ctypes.data, _completed_buf.shape[0],
+                                              ctypes.byref(n)), srv)
+        out.extend(_completed_buf[: n.value].tolist())
+        if n.value < _completed_buf.shape[0]:
+            return out
 
 
 def lk_server_get_stats(srv) -> dict:

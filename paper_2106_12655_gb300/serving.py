@@ -91,7 +91,7 @@ def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0
             pending[t] = (nxt, k)
             nxt += 1
         lk.lk_server_step(srv, wait=False)
-        for t in list(pending):
+        for t in lk.lk_server_completed(srv):
             if lk.lk_server_poll(srv, t, None, None, status):
                 i, k = pending.pop(t)
                 bad += int(np.count_nonzero(status[:plan[i][1].shape[0]]))

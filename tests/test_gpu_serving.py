@@ -157,3 +157,36 @@ def test_resident_geometry_updated_between_requests():
     finally:
         lk.lk_server_destroy(srv)
         lk.lk_destroy(ctx)
+
+
+def test_completed_reports_each_finished_ticket_once():
+    gs = scenes()[:3]
+    ctxs = [lk.lk_create(g.vertices, g.offsets) for g in gs]
+    srv = lk.lk_server_create(None)
+    try:
+        sizes, tickets = {}, []
+        for k, g in enumerate(gs):
+            for w in range(3):
+                p = np.ascontiguousarray(g.pairs[w::3])
+                t = lk.lk_server_submit(srv, ctxs[k], p)
+                sizes[t] = (p.shape[0], k, p)
+                tickets.append(t)
+        seen = []
+        for _ in range(100000):
+            lk.lk_server_step(srv, wait=True)
+            seen += lk.lk_server_completed(srv)
+            if len(seen) == len(tickets):
+                break
+        assert sorted(seen) == sorted(tickets) and len(set(seen)) == len(seen)
+        assert lk.lk_server_completed(srv) == []
+        for t in seen:
+            n, k, p = sizes[t]
+            out = np.zeros(n, np.int32), np.zeros(n), np.zeros(n, np.int32)
+            assert lk.lk_server_poll(srv, t, *out)
+            ref = alone(ctxs[k], p)
+            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[2], ref[2])
+            assert np.array_equal(out[1], ref[1])
+    finally:
+        lk.lk_server_destroy(srv)
+        for c in ctxs:
+            lk.lk_destroy(c)
