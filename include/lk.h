@@ -233,7 +233,7 @@ lk_status lk_verify_expected(lk_ctx* ctx, const int32_t* loop_pairs, const int32
  * Autotuner for the work split (the batching of Algorithm 1's loop over P
  * into work items; the paper launches one kernel per pair, Sec. 3.4).
  * For each size class present in loop_pairs -- a class is the pair
- * (ceil(log2 N_rows), ceil(log2 N_cols)) of the longer and shorter loop --
+ * (ceil(log2 N_rows), ceil(log2 N_cols)) of the row and column loop --
  * times the mixed-precision verify of up to 4096 of that class's pairs
  * (at most 2^31 segment pairs) at each candidate work-item height
  * (32 ... 65536 row segments) with CUDA events, and records the fastest in the

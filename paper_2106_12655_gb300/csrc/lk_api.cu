@@ -222,10 +222,11 @@ int default_tile_rows(int64_t n_rows, int64_t n_cols, int tile_cols, int user_ro
 }
 
 // Work items of a pair list.  Loop a of a pair plays gamma_1 of Eq. 4 and loop
-// b gamma_2; the term is symmetric under exchanging them (Eq. 1), so the
-// longer loop becomes the row loop (iterated) and the other the column loop
-// (spread over lanes).  The tiling of a pair depends on its two sizes only, so
-// a pair's result does not depend on the rest of the batch.
+// b gamma_2; the term is symmetric under exchanging them (Eq. 1), so either
+// can be the row loop (iterated) and the other the column loop (spread over
+// lanes in tiles of tile_cols): the one whose column tiles waste fewer lanes,
+// else the longer one.  The tiling of a pair depends on its two sizes only,
+// so a pair's result does not depend on the rest of the batch.
 lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
     const bool f64 = ctx->opt.precision == LK_ALL_F64;
     const int tile_cols = f64 ? lk::kF64TileCols : lk::kTileCols;
@@ -254,7 +255,11 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
         }
         const int64_t na = ctx->h_offsets[a + 1] - ctx->h_offsets[a];
         const int64_t nb = ctx->h_offsets[b + 1] - ctx->h_offsets[b];
-        const bool a_rows = na >= nb;
+        // The orientation that sweeps fewer cells including the padding of the
+        // last column tile; on a tie the longer loop is the row loop.
+        const int64_t cells_a_rows = na * ((nb + tile_cols - 1) / tile_cols);
+        const int64_t cells_b_rows = nb * ((na + tile_cols - 1) / tile_cols);
+        const bool a_rows = cells_a_rows != cells_b_rows ? cells_a_rows < cells_b_rows : na >= nb;
         t.row_loop = a_rows ? a : b;
         t.col_loop = a_rows ? b : a;
         t.n_rows = (int32_t)(a_rows ? na : nb);
