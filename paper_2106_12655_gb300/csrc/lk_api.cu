@@ -448,8 +448,9 @@ lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStrea
             lk::launch_sweep_mixed(a, false, pk.n_acc_items, pk.n_items, ws.counters.p + 4,
                                    ctx->num_sms * lk::sweep_mixed_blocks_per_sm(false), s);
             if (ctx->opt.timing) LK_CUDA(ctx, record_event(ws.ev1, s));
-            lk::launch_careful_chunks(a, ctx->num_sms * lk::careful_chunk_blocks_per_sm(), s);
-            lk::launch_sweep_careful(a, ctx->num_sms * lk::sweep_careful_blocks_per_sm(), s);
+            const bool fast = pk.n_items > pk.n_acc_items, acc = pk.n_acc_items > 0;
+            lk::launch_careful_chunks(a, fast, acc, ctx->num_sms * lk::careful_chunk_blocks_per_sm(), s);
+            lk::launch_sweep_careful(a, fast, acc, ctx->num_sms * lk::sweep_careful_blocks_per_sm(), s);
             lk::launch_near_fix(a, ctx->num_sms * 4, s);
         }
     }
@@ -1387,8 +1388,9 @@ lk_status launch_wave(lk_server* s) {
     lk::launch_wave(s->d_segs[slot] + n_acc, n_fast, fast_items, false, cnt + 1,
                     s->num_sms * lk::wave_blocks_per_sm(false), st);
     for (Request* r : completing) {
-        lk::launch_careful_chunks(r->args, s->num_sms * lk::careful_chunk_blocks_per_sm(), st);
-        lk::launch_sweep_careful(r->args, s->num_sms * lk::sweep_careful_blocks_per_sm(), st);
+        const bool fast = r->pk.n_items > r->pk.n_acc_items, acc = r->pk.n_acc_items > 0;
+        lk::launch_careful_chunks(r->args, fast, acc, s->num_sms * lk::careful_chunk_blocks_per_sm(), st);
+        lk::launch_sweep_careful(r->args, fast, acc, s->num_sms * lk::sweep_careful_blocks_per_sm(), st);
         lk::launch_near_fix(r->args, s->num_sms * 4, st);
         lk::ReduceArgs ra{};
         ra.tasks = r->ws.tasks.p;

@@ -141,8 +141,10 @@ void launch_pair_frames(PairTask* tasks, int64_t n_tasks, const double* aabb, cu
 void launch_sweep_mixed(const SweepArgs& a, bool accurate, int64_t item_lo, int64_t item_hi,
                         unsigned long long* counter, int grid, cudaStream_t s);
 void launch_sweep_f64(const SweepArgs& a, int grid, cudaStream_t s);
-void launch_sweep_careful(const SweepArgs& a, int grid, cudaStream_t s);
-void launch_careful_chunks(const SweepArgs& a, int grid, cudaStream_t s);
+// The careful passes of each arithmetic variant; a variant without work items
+// in the call is not launched.
+void launch_sweep_careful(const SweepArgs& a, bool fast, bool accurate, int grid, cudaStream_t s);
+void launch_careful_chunks(const SweepArgs& a, bool fast, bool accurate, int grid, cudaStream_t s);
 int careful_chunk_blocks_per_sm();
 void launch_near_fix(const SweepArgs& a, int grid, cudaStream_t s);
 void launch_wave(const WaveSeg* segs, int n_segs, int64_t n_items, bool accurate,
