@@ -190,3 +190,26 @@ def test_completed_reports_each_finished_ticket_once():
         lk.lk_server_destroy(srv)
         for c in ctxs:
             lk.lk_destroy(c)
+
+
+def test_fp64_list_overflow_is_reported_and_exact():
+    """A server whose per-request FP64 list holds 8 entries evaluates the rest
+    in place: the results must equal lk_verify's, and the statistics must show
+    the overflow."""
+    g = W.serving_pile(77, 400, 400)            # 64-256-segment rings: many near segment pairs
+    ctx = lk.lk_create(g.vertices, g.offsets)
+    o = lk.lk_server_default_options()
+    o.near_capacity = 8
+    srv = lk.lk_server_create(o)
+    try:
+        pairs = np.ascontiguousarray(g.pairs)
+        t = lk.lk_server_submit(srv, ctx, pairs)
+        res = drain(srv, [t], {t: pairs.shape[0]})[t]
+        ref = alone(ctx, pairs)
+        assert np.array_equal(res[0], ref[0]) and np.array_equal(res[2], ref[2])
+        assert np.abs(res[1] - ref[1]).max() <= 1e-12
+        st = lk.lk_server_get_stats(srv)
+        assert st["near_overflow"] > 0 and st["careful_chunks"] > 0
+    finally:
+        lk.lk_server_destroy(srv)
+        lk.lk_destroy(ctx)
