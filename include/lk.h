@@ -129,7 +129,8 @@ lk_status lk_create(lk_ctx** out, const void* vertices, lk_dtype vdtype, int64_t
 /*
  * Replace the resident vertices (is_delta = 0) or add a displacement to each
  * (is_delta = 1), keeping the loop structure: one simulation step of the
- * verification loop of Sec. 5 ("compare M_t with M_0").
+ * verification loop of Sec. 4.3 (a linking certificate before and after a
+ * deformation).
  *  data : [n_vertices][3] of dtype, host or device.
  * Enqueued on cuda_stream; later work on that stream sees the new geometry.
  * Errors: LK_ERR_ARG, LK_ERR_CUDA.  No zero-length check is made here; a
@@ -197,7 +198,7 @@ const char* lk_last_error(const lk_ctx* ctx);
  * A plan fixes one pair list and captures the whole verify (pair set-up,
  * persistent tile sweep, FP64 recompute, per-pair reduction) as a CUDA graph,
  * so that a simulation loop re-verifies the same certificate after each
- * lk_update with one graph launch (Sec. 5 verification loop; Algorithm 1).
+ * lk_update with one graph launch (Sec. 4.3 verification loop; Algorithm 1).
  *  loop_pairs : copied at creation; later changes to the caller's array are
  *               not seen.
  * lk_plan_run writes the same outputs as lk_verify (same rules for host and
@@ -252,7 +253,7 @@ lk_status lk_tune_set(lk_ctx* ctx, const int32_t* entries, int64_t n_entries);
 
 /*
  * Serving: continuous batching of verify requests over resident geometry
- * (the per-frame verification of Sec. 5's simulation examples, as a service).
+ * (the per-frame verification of Sec. 4.3's simulation examples, as a service).
  * A server owns a device arena of arena_bytes (requests are admitted only
  * while their work buffers fit in it), a pinned host arena of host_bytes for
  * results, and a FIFO of submitted requests.  lk_server_step retires finished
