@@ -90,6 +90,8 @@ def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0
             sc.in_flight += 1
             pending[t] = (nxt, k)
             nxt += 1
+            # launch work as soon as it is admitted, not after a burst of submits
+            lk.lk_server_step(srv, wait=False)
         lk.lk_server_step(srv, wait=False)
         for t in lk.lk_server_completed(srv):
             if lk.lk_server_poll(srv, t, None, None, status):
