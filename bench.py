@@ -192,6 +192,49 @@ def pls_block(scenes):
     return out
 
 
+def counting_crossings_block(g, v, off, pairs_d, lk_ref, stream, flush, steps=20):
+    """The counting-crossings method (LK_METHOD_CC) on the same sheet and graph
+    protocol: device time per step, and whether its linking numbers equal the
+    direct sum's.  Its results are exact integers where the crossings decide a
+    pair."""
+    import torch
+    from paper_2106_12655_gb300 import lk
+
+    n = g.pairs.shape[0]
+    o = lk.lk_default_options()
+    o.method = lk.LK_METHOD_CC
+    o.timing = 1
+    ctx = lk.lk_create(v, off, o, stream)
+    plan = lk.lk_plan_create(ctx, pairs_d, stream)
+    lo = torch.zeros(n, dtype=torch.int32, device=v.device)
+    raw = torch.zeros(n, dtype=torch.float64, device=v.device)
+    st = torch.zeros(n, dtype=torch.int32, device=v.device)
+    ms, sweep = [], []
+    try:
+        for k in range(steps + 3):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lk.lk_plan_run(plan, lo, raw, st, stream, ctx=ctx)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 3:
+                ms.append(e0.elapsed_time(e1))
+                sweep.append(lk.lk_get_stats(ctx)["sweep_ms"])
+        stats = lk.lk_get_stats(ctx)
+        lo_h, raw_h, st_h = lo.cpu().numpy(), raw.cpu().numpy(), st.cpu().numpy()
+    finally:
+        lk.lk_plan_destroy(plan)
+        lk.lk_destroy(ctx)
+    med = statistics.median(ms)
+    return {"value": g.segment_pairs() / (med / 1e3), "unit": UNIT, "ms_per_step": med,
+            "sweep_ms": statistics.median(sweep), "candidates": stats["cc_candidates"],
+            "fallback_pairs": stats["cc_fallback_pairs"],
+            "lk_equal_direct_sum": bool(np.array_equal(lo_h, lk_ref)),
+            "exact_integer_raw": bool(np.all(raw_h == lo_h)), "all_status_ok": bool(np.all(st_h == 0))}
+
+
 def cpu_baseline(g):
     from oracle import oracle as O
 
@@ -393,6 +436,8 @@ def run_ours(args):
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clk, "wall_s_timed_region": wall,
     }
+    if world == 1:
+        line["counting_crossings"] = counting_crossings_block(g, v, off, pairs_d, lk_host, stream, flush)
     if not args.no_serving and world == 1:
         line["serving"] = serving_block(args)
     if not args.no_cpu_baseline and world == 1:

@@ -62,6 +62,19 @@ typedef enum {
     LK_ALL_F64 = 1
 } lk_precision;
 
+typedef enum {
+    /* direct summation of Eq. 4 over every segment pair (the default) */
+    LK_METHOD_DS = 0,
+    /* counting crossings of a projection (Sec. 3.4, Method 1; Algorithm 4): an
+     * FP32 sweep over every segment pair finds candidate crossings, FP64
+     * decides them, and the count of signed crossings gives the linking
+     * number exactly; a pair whose projection is not regular within FP64
+     * rounding (or whose candidates overflow cc_capacity) is computed by the
+     * direct sum in the same call.  raw_out then holds the exact integer.
+     * Requires precision LK_MIXED; the server always uses LK_METHOD_DS. */
+    LK_METHOD_CC = 1
+} lk_method;
+
 typedef struct lk_options {
     int precision;       /* lk_precision, default LK_MIXED */
     double near_ratio;   /* tau >= 3: a segment pair whose nearest corner distance (the smallest
@@ -84,6 +97,9 @@ typedef struct lk_options {
                             (Appendix B: one arctangent per column and chunk); a chunk whose
                             nearest corner is within 4.5 segment lengths is swept per pair
                             instead.  0 = always accurate; default 1<<22 */
+    int method;          /* lk_method, default LK_METHOD_DS */
+    int cc_capacity;     /* LK_METHOD_CC: candidate crossings per verify (default 1<<18); pairs
+                            whose candidates do not fit are computed by the direct sum */
 } lk_options;
 
 typedef struct lk_stats {
@@ -97,6 +113,8 @@ typedef struct lk_stats {
     int64_t careful_items;    /* whole items swept again with per-pair tests (chunk list full) */
     double sweep_ms;          /* bulk sweep kernel time (options.timing = 1), else -1 */
     int64_t careful_chunks;   /* 32-row chunks swept again with per-pair tests */
+    int64_t cc_candidates;    /* LK_METHOD_CC: candidate crossings found by the FP32 sweep */
+    int64_t cc_fallback_pairs;/* LK_METHOD_CC: pairs the crossings could not decide (direct sum) */
 } lk_stats;
 
 typedef struct lk_ctx lk_ctx;

@@ -100,7 +100,11 @@ struct Workspace {
     DevBuf<int> flags;
     DevBuf<unsigned long long> counters;  // [0] accurate-sweep counter, [1] overflow,
                                           // [2] u32 careful_count, careful_counter,
-                                          // [3] u32 near_count, unused, [4] fast-sweep / f64 counter
+                                          // [3] u32 near_count, unused, [4] fast-sweep / f64 counter,
+                                          // [5], [6] chunk pass, [8] crossing sweep counter,
+                                          // [9] u32 crossing candidates
+    DevBuf<NearEntry> cc_list;            // counting crossings: candidates (method CC only)
+    DevBuf<int> cc_half;
     DevBuf<int32_t> lk;
     DevBuf<double> raw;
     DevBuf<int32_t> status;
@@ -120,6 +124,7 @@ struct Workspace {
         tasks.release(); item_begin.release(); item_task.release(); partial.release();
         careful_items.release(); careful_chunks.release(); item_fix.release(); near_list.release(); fix_acc.release(); fp64_count.release();
         flags.release(); counters.release(); lk.release(); raw.release(); status.release();
+        cc_list.release(); cc_half.release();
     }
 };
 
@@ -145,6 +150,8 @@ struct lk_ctx {
     const unsigned long long* stats_fp64 = nullptr;
     const unsigned long long* stats_overflow = nullptr;
     const unsigned int* stats_careful = nullptr;
+    const int* stats_flags = nullptr;            // per-pair flags of the last verify (CC fallbacks)
+    bool stats_cc = false;
     cudaEvent_t stats_ev0 = nullptr, stats_ev1 = nullptr;
     cudaStream_t stats_stream = nullptr;
     std::map<uint32_t, int> tune;   // size class -> tile rows chosen by lk_autotune
@@ -336,9 +343,10 @@ size_t chunk_capacity(const lk_options& o, int64_t n_chunks);
 
 size_t workspace_bytes(const lk_ctx* ctx, int64_t n_tasks, int64_t n_items, int64_t n_chunks) {
     const size_t near = (size_t)std::max(0, ctx->opt.near_capacity);
-    return n_tasks * (sizeof(PairTask) + 8 + 8 + 8 + 4 + 4 + 8 + 4) + n_items * (4 + 8 + 8 + 8) +
+    const size_t cc = ctx->opt.method == LK_METHOD_CC ? (size_t)std::max(1, ctx->opt.cc_capacity) : 0;
+    return n_tasks * (sizeof(PairTask) + 8 + 8 + 8 + 4 + 4 + 8 + 4 + (cc ? 4 : 0)) + n_items * (4 + 8 + 8 + 8) +
            chunk_capacity(ctx->opt, n_chunks) * sizeof(lk::CarefulChunk) +
-           near * sizeof(NearEntry) + 64;
+           (near + cc) * sizeof(NearEntry) + 80;
 }
 
 // Entries of the chunk hand-over list: every chunk of the batch, at most the
@@ -363,7 +371,11 @@ lk_status ensure_workspace(lk_ctx* ctx, Workspace& ws, int64_t n_tasks, int64_t 
     LK_CUDA(ctx, ws.fix_acc.ensure(nt));
     LK_CUDA(ctx, ws.fp64_count.ensure(nt));
     LK_CUDA(ctx, ws.flags.ensure(nt));
-    LK_CUDA(ctx, ws.counters.ensure(8));
+    LK_CUDA(ctx, ws.counters.ensure(10));
+    if (ctx->opt.method == LK_METHOD_CC) {
+        LK_CUDA(ctx, ws.cc_list.ensure((size_t)std::max(1, ctx->opt.cc_capacity)));
+        LK_CUDA(ctx, ws.cc_half.ensure(nt));
+    }
     LK_CUDA(ctx, ws.lk.ensure(nt));
     LK_CUDA(ctx, ws.raw.ensure(nt));
     LK_CUDA(ctx, ws.status.ensure(nt));
@@ -410,6 +422,13 @@ lk::SweepArgs sweep_args(const lk_ctx* ctx, Workspace& ws, const Packed& pk) {
     a.fp64_count = ws.fp64_count.p;
     a.flags = ws.flags.p;
     a.near_ratio_sq = (float)(ctx->opt.near_ratio * ctx->opt.near_ratio);
+    if (ctx->opt.method == LK_METHOD_CC) {
+        a.cc_list = ws.cc_list.p;
+        a.cc_count = reinterpret_cast<unsigned int*>(ws.counters.p + 9);
+        a.cc_capacity = (int)std::min<size_t>(ws.cc_list.cap, (size_t)INT32_MAX);
+        a.cc_half = ws.cc_half.p;
+        a.skip_unflagged = 1;
+    }
     return a;
 }
 
@@ -427,8 +446,10 @@ cudaError_t record_event(cudaEvent_t ev, cudaStream_t s) {
 lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStream_t s) {
     const int64_t n = (int64_t)pk.tasks.size();
     if (n == 0) return LK_OK;
-    LK_CUDA(ctx, cudaMemsetAsync(ws.counters.p, 0, 8 * sizeof(unsigned long long), s));
+    LK_CUDA(ctx, cudaMemsetAsync(ws.counters.p, 0, 10 * sizeof(unsigned long long), s));
     LK_CUDA(ctx, cudaMemsetAsync(ws.fix_acc.p, 0, n * sizeof(unsigned long long), s));
+    const bool cc = ctx->opt.method == LK_METHOD_CC;
+    if (cc) LK_CUDA(ctx, cudaMemsetAsync(ws.cc_half.p, 0, n * sizeof(int), s));
     LK_CUDA(ctx, cudaMemsetAsync(ws.fp64_count.p, 0, n * sizeof(unsigned long long), s));
     LK_CUDA(ctx, cudaMemsetAsync(ws.flags.p, 0, n * sizeof(int), s));
     if (pk.n_items > 0)
@@ -443,6 +464,12 @@ lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStrea
             if (ctx->opt.timing) LK_CUDA(ctx, record_event(ws.ev1, s));
         } else {
             if (ctx->opt.timing) LK_CUDA(ctx, record_event(ws.ev0, s));
+            if (cc) {
+                // counting crossings first; the direct sum then runs only on the
+                // pairs it flagged (its sweeps skip every other item)
+                lk::launch_cc_sweep(a, ws.counters.p + 8, ctx->num_sms * lk::cc_sweep_blocks_per_sm(), s);
+                lk::launch_cc_resolve(a, ctx->num_sms * 4, s);
+            }
             lk::launch_sweep_mixed(a, true, 0, pk.n_acc_items, ws.counters.p + 0,
                                    ctx->num_sms * lk::sweep_mixed_blocks_per_sm(true), s);
             lk::launch_sweep_mixed(a, false, pk.n_acc_items, pk.n_items, ws.counters.p + 4,
@@ -456,6 +483,7 @@ lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStrea
     }
     lk::ReduceArgs r{};
     r.tasks = ws.tasks.p;
+    r.cc_half = cc ? ws.cc_half.p : nullptr;
     r.item_begin = ws.item_begin.p;
     r.partial = ws.partial.p;
     r.fix_acc = ws.fix_acc.p;
@@ -501,6 +529,8 @@ void note_stats(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStream_t s) {
     ctx->stats_fp64 = ws.fp64_count.p;
     ctx->stats_overflow = ws.counters.p + 1;
     ctx->stats_careful = reinterpret_cast<const unsigned int*>(ws.counters.p + 2);
+    ctx->stats_flags = ws.flags.p;
+    ctx->stats_cc = ctx->opt.method == LK_METHOD_CC && ws.cc_list.p != nullptr;
     ctx->stats_ev0 = (ctx->opt.timing && pk.n_items > 0) ? ws.ev0 : nullptr;
     ctx->stats_ev1 = ws.ev1;
     ctx->stats_stream = s;
@@ -537,6 +567,8 @@ void lk_default_options(lk_options* opt) {
     opt->timing = 0;
     opt->chunk_capacity = 1 << 20;
     opt->accurate_threshold = (int64_t)1 << 22;
+    opt->method = LK_METHOD_DS;
+    opt->cc_capacity = 1 << 18;
 }
 
 const char* lk_last_error(const lk_ctx* ctx) {
@@ -558,8 +590,11 @@ lk_status lk_create(lk_ctx** out, const void* vertices, lk_dtype vdtype, int64_t
     if (opt) o = *opt;
     if (!(o.near_ratio >= 3.0) || !(o.int_tol > 0.0 && o.int_tol < 0.5) ||
         (o.precision != LK_MIXED && o.precision != LK_ALL_F64) || o.tile_rows < 0 ||
-        o.near_capacity < 1 || o.accurate_threshold < 0 || o.chunk_capacity < 1)
-        return fail(nullptr, LK_ERR_ARG, "lk_create: invalid options (near_ratio >= 3, 0 < int_tol < 0.5)");
+        o.near_capacity < 1 || o.accurate_threshold < 0 || o.chunk_capacity < 1 ||
+        (o.method != LK_METHOD_DS && o.method != LK_METHOD_CC) || o.cc_capacity < 1 ||
+        (o.method == LK_METHOD_CC && o.precision != LK_MIXED))
+        return fail(nullptr, LK_ERR_ARG,
+                    "lk_create: invalid options (near_ratio >= 3, 0 < int_tol < 0.5; LK_METHOD_CC needs LK_MIXED)");
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
     // Host copies for validation.
@@ -784,10 +819,23 @@ lk_status lk_get_stats(lk_ctx* ctx, lk_stats* out) {
         LK_CUDA(ctx, cudaMemcpy(&ov, ctx->stats_overflow, sizeof ov, cudaMemcpyDeviceToHost));
         ctx->stats.fp64_pairs = (int64_t)std::accumulate(c.begin(), c.end(), 0ull);
         ctx->stats.near_overflow = (int64_t)ov;
-        unsigned int u32[8] = {};
-        LK_CUDA(ctx, cudaMemcpy(u32, ctx->stats_careful, sizeof u32, cudaMemcpyDeviceToHost));
+        unsigned int u32[16] = {};
+        LK_CUDA(ctx, cudaMemcpy(u32, ctx->stats_careful, ctx->stats_cc ? 16 * sizeof(unsigned int)
+                                                                     : 8 * sizeof(unsigned int),
+                                cudaMemcpyDeviceToHost));
         ctx->stats.careful_items = u32[0];
         ctx->stats.careful_chunks = u32[6];
+        ctx->stats.cc_candidates = 0;
+        ctx->stats.cc_fallback_pairs = 0;
+        if (ctx->stats_cc) {
+            ctx->stats.cc_candidates = u32[14];          // low half of counters[9]
+            std::vector<int> fl((size_t)std::max<int64_t>(ctx->stats_tasks, 1), 0);
+            if (ctx->stats_tasks > 0)
+                LK_CUDA(ctx, cudaMemcpy(fl.data(), ctx->stats_flags, ctx->stats_tasks * sizeof(int),
+                                        cudaMemcpyDeviceToHost));
+            for (int64_t t = 0; t < ctx->stats_tasks; ++t)
+                ctx->stats.cc_fallback_pairs += (fl[(size_t)t] & lk::kFlagCcFallback) ? 1 : 0;
+        }
         ctx->stats.sweep_ms = -1.0;
         if (ctx->stats_ev0) {
             float ms = 0.0f;
@@ -1015,7 +1063,7 @@ extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, in
     bind(ws.fix_acc, (size_t)kNoallocMaxPairs);
     bind(ws.fp64_count, (size_t)kNoallocMaxPairs);
     bind(ws.flags, (size_t)kNoallocMaxPairs);
-    bind(ws.counters, 8);
+    bind(ws.counters, 10);
     bind(ws.lk, (size_t)kNoallocMaxPairs);
     bind(ws.raw, (size_t)kNoallocMaxPairs);
     bind(ws.status, (size_t)kNoallocMaxPairs);

@@ -36,6 +36,7 @@ constexpr double kChunkFixScale = 4294967296.0;  // 2^32
 
 // Per-pair flag bits.
 constexpr int kFlagIntersect = 1;
+constexpr int kFlagCcFallback = 2;   // counting crossings could not decide the pair: direct sum
 
 // One loop pair of a verify call, laid out for the device.
 //
@@ -111,6 +112,12 @@ struct SweepArgs {
     unsigned long long* item_fix;  // [n_items] fixed-point 2^-32 rad: careful chunk sums
     int* flags;                    // [n_tasks] kFlag* bits
     float near_ratio_sq;           // tau^2
+    // Counting crossings (lk_options.method = LK_METHOD_CC).
+    NearEntry* cc_list;            // candidate crossings (task, j, i) for the FP64 resolve
+    unsigned int* cc_count;        // [1] entries of cc_list (may exceed capacity)
+    int cc_capacity;
+    int* cc_half;                  // [n_tasks] twice the linking number by crossings
+    int skip_unflagged;            // direct-sum sweeps: only items of pairs flagged kFlagCcFallback
 };
 
 // One request's contiguous run of items inside a serving wave.
@@ -122,6 +129,7 @@ struct WaveSeg {
 
 struct ReduceArgs {
     const PairTask* tasks;
+    const int* cc_half;            // counting crossings: non-null selects it for unflagged pairs
     const int64_t* item_begin;
     const double* partial;
     const unsigned long long* item_fix;   // may be null
@@ -153,6 +161,12 @@ int wave_blocks_per_sm(bool accurate);
 void launch_reduce(const ReduceArgs& a, cudaStream_t s);
 void launch_update(Vtx* V, const void* data, int dtype, int is_delta, int64_t n, cudaStream_t s);
 int sweep_mixed_blocks_per_sm(bool accurate);
+
+// Counting crossings (lk_kernels.cu): the FP32 candidate sweep over all items
+// and the FP64 resolve of the candidates.
+void launch_cc_sweep(const SweepArgs& a, unsigned long long* counter, int grid, cudaStream_t s);
+void launch_cc_resolve(const SweepArgs& a, int grid, cudaStream_t s);
+int cc_sweep_blocks_per_sm();
 
 // Potential link search (lk_pls.cu).
 void launch_pls_keys(const double* aabb, int64_t n_loops, long long* keys, cudaStream_t s);

@@ -28,6 +28,8 @@ LK_F32 = 0
 LK_F64 = 1
 LK_MIXED = 0
 LK_ALL_F64 = 1
+LK_METHOD_DS = 0
+LK_METHOD_CC = 1
 
 STATUS_NAMES = {0: "LK_OK", 1: "LK_ERR_ARG", 2: "LK_ERR_ZERO_SEGMENT", 3: "LK_ERR_INTERSECT",
                 4: "LK_ERR_NONINTEGER", 5: "LK_ERR_OOM", 6: "LK_ERR_TIMEOUT", 7: "LK_ERR_CUDA",
@@ -45,7 +47,8 @@ class lk_options(ctypes.Structure):
                 ("int_tol", ctypes.c_double), ("mem_budget", ctypes.c_size_t),
                 ("tile_rows", ctypes.c_int), ("near_capacity", ctypes.c_int),
                 ("timing", ctypes.c_int), ("chunk_capacity", ctypes.c_int),
-                ("accurate_threshold", ctypes.c_int64)]
+                ("accurate_threshold", ctypes.c_int64), ("method", ctypes.c_int),
+                ("cc_capacity", ctypes.c_int)]
 
 
 class lk_stats(ctypes.Structure):
@@ -53,7 +56,8 @@ class lk_stats(ctypes.Structure):
                 ("segment_pairs", ctypes.c_int64), ("fp64_pairs", ctypes.c_int64),
                 ("near_overflow", ctypes.c_int64), ("tile_rows", ctypes.c_int32),
                 ("tile_cols", ctypes.c_int32), ("careful_items", ctypes.c_int64),
-                ("sweep_ms", ctypes.c_double), ("careful_chunks", ctypes.c_int64)]
+                ("sweep_ms", ctypes.c_double), ("careful_chunks", ctypes.c_int64),
+                ("cc_candidates", ctypes.c_int64), ("cc_fallback_pairs", ctypes.c_int64)]
 
 
 class lk_server_options(ctypes.Structure):

@@ -50,6 +50,7 @@ def test_default_options(lib):
     assert o.near_ratio == 3.0
     assert o.int_tol == 0.1
     assert o.near_capacity == 1 << 20
+    assert o.method == lk.LK_METHOD_DS and o.cc_capacity == 1 << 18
 
 
 def _create_status(v, off, opt=None):
@@ -68,6 +69,13 @@ def test_create_rejects_bad_geometry_before_device_work(lib):
     assert _create_status(bad, np.array([0, 5, 10], np.int64)) == lk.LK_ERR_ARG
     o = lk.lk_default_options()
     o.near_ratio = 2.5
+    assert _create_status(v, np.array([0, 5, 10], np.int64), o) == lk.LK_ERR_ARG
+    o = lk.lk_default_options()
+    o.method = lk.LK_METHOD_CC
+    o.precision = lk.LK_ALL_F64                       # counting crossings needs LK_MIXED
+    assert _create_status(v, np.array([0, 5, 10], np.int64), o) == lk.LK_ERR_ARG
+    o = lk.lk_default_options()
+    o.method = 7
     assert _create_status(v, np.array([0, 5, 10], np.int64), o) == lk.LK_ERR_ARG
 
 

@@ -1,0 +1,128 @@
+"""Counting crossings (LK_METHOD_CC; Sec. 3.4, Method 1, Algorithm 4): the
+linking numbers must equal the FP64 direct-sum oracle's exactly, and a pair
+decided by its crossings returns the exact integer as its raw value.  Pairs
+the projection cannot decide (forced here by a tiny candidate list) fall
+back to the direct sum in the same call."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2106_12655_gb300 import lk
+from paper_2106_12655_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_12655_gb300 import build as B
+
+    B.build()
+    lk.load()
+
+
+def run_cc(g, pairs=None, **opts):
+    pairs = g.pairs if pairs is None else np.asarray(pairs, np.int32).reshape(-1, 2)
+    o = lk.lk_default_options()
+    o.method = lk.LK_METHOD_CC
+    for k, v in opts.items():
+        setattr(o, k, v)
+    stream = torch.cuda.current_stream()
+    ctx = lk.lk_create(np.ascontiguousarray(g.vertices), g.offsets, o, stream)
+    try:
+        n = pairs.shape[0]
+        out = np.zeros(n, np.int32), np.zeros(n), np.zeros(n, np.int32)
+        lk.lk_verify(ctx, np.ascontiguousarray(pairs), *out, stream)
+        st = lk.lk_get_stats(ctx)
+    finally:
+        lk.lk_destroy(ctx)
+    return out + (st,)
+
+
+def check(g, pairs=None, **opts):
+    pairs = g.pairs if pairs is None else np.asarray(pairs, np.int32).reshape(-1, 2)
+    lk_o, raw, status, st = run_cc(g, pairs, **opts)
+    ref = O.round_lk(O.link_pairs(g.vertices, g.offsets, pairs)).astype(np.int32)
+    assert np.all(status == lk.LK_OK), np.unique(status, return_counts=True)
+    assert np.array_equal(lk_o, ref), np.nonzero(lk_o != ref)
+    return lk_o, raw, st
+
+
+@pytest.mark.parametrize("name", ["ring_chain", "chainmail", "torus_small", "whitehead", "ribbon", "hopf"])
+def test_cc_matches_oracle_and_is_exact(name):
+    g = {"ring_chain": lambda: W.ring_chain(),
+         "chainmail": lambda: W.chainmail(),
+         "torus_small": lambda: W.torus_link(5, 7, 3000, dtype=np.float32, n2=2711),
+         "whitehead": lambda: W.whitehead(),
+         "ribbon": lambda: W.double_helix_ribbon(25, 6000),
+         "hopf": lambda: W.hopf(24, 30)}[name]()
+    lk_o, raw, st = check(g)
+    # decided by crossings: the raw value is the integer itself
+    assert st["cc_fallback_pairs"] == 0
+    assert np.array_equal(raw, lk_o.astype(np.float64))
+    assert st["fp64_pairs"] == 0
+
+
+def test_cc_knit_yarn_sampled_pairs():
+    g = W.knit_yarn()
+    rng = np.random.default_rng(4)
+    pick = np.sort(rng.choice(g.pairs.shape[0], 12, replace=False))
+    lk_o, raw, st = check(g, g.pairs[pick])
+    assert np.array_equal(raw, lk_o.astype(np.float64))
+
+
+def test_cc_large_torus_closed_form():
+    g = W.torus_link(31, 37, 250_000, dtype=np.float32)
+    lk_o, raw, status, st = run_cc(g)
+    assert status[0] == lk.LK_OK and lk_o[0] == -31 * 37
+    assert st["cc_fallback_pairs"] == 0 and raw[0] == -31 * 37
+
+
+def test_cc_random_polygons_against_exact_crossings():
+    import crossings as C
+
+    rng = np.random.default_rng(12)
+    loops, pairs, expect = [], [], []
+    for k in range(40):
+        a = rng.normal(size=(rng.integers(4, 30), 3))
+        b = rng.normal(size=(rng.integers(4, 30), 3)) + rng.normal(scale=0.3, size=3)
+        try:
+            lam = C.linking_number_exact(a, b, rng=rng)
+        except C.Intersecting:
+            continue
+        base = len(loops)
+        loops += [a, b]
+        pairs.append([base, base + 1])
+        expect.append(lam)
+    g = W.from_loops(loops, dtype=np.float64, pairs=pairs)
+    lk_o, raw, status, st = run_cc(g)
+    assert np.all(status == lk.LK_OK)
+    assert np.array_equal(lk_o, np.asarray(expect, np.int32))
+
+
+def test_cc_fallback_to_direct_sum():
+    """A one-entry candidate list: every pair with more than one candidate is
+    computed by the direct sum instead; the linking numbers do not change."""
+    g = W.chainmail(rows=6, cols=10, dtype=np.float64)
+    lk_full, raw_full, _ = check(g)
+    lk_o, raw, st = check(g, cc_capacity=1)
+    assert np.array_equal(lk_o, lk_full)
+    fell_back = raw != lk_o.astype(np.float64)
+    assert fell_back.any() and not fell_back.all()
+    assert st["cc_fallback_pairs"] == int(fell_back.sum())
+    ref = O.link_pairs(g.vertices, g.offsets, g.pairs)
+    assert np.abs(raw[fell_back] - ref[fell_back]).max() <= 1e-6
+
+
+def test_cc_reports_intersections():
+    t = np.arange(64) * 2 * np.pi / 64
+    a = np.stack([np.cos(t), np.sin(t), 0 * t], 1)
+    b = np.stack([np.cos(t), 0 * t, np.sin(t)], 1)          # shares vertices (+-1,0,0) with a
+    c = np.stack([5 + np.cos(t), np.sin(t), 0 * t], 1)
+    g = W.from_loops([a, b, c], pairs=[[0, 1], [0, 2]])
+    lk_o, raw, status, st = run_cc(g)
+    assert status[0] == lk.LK_ERR_INTERSECT and lk_o[0] == 0
+    assert status[1] == lk.LK_OK and lk_o[1] == 0 and raw[1] == 0.0
