@@ -424,7 +424,7 @@ lk::SweepArgs sweep_args(const lk_ctx* ctx, Workspace& ws, const Packed& pk) {
     a.near_ratio_sq = (float)(ctx->opt.near_ratio * ctx->opt.near_ratio);
     if (ctx->opt.method == LK_METHOD_CC) {
         a.cc_list = ws.cc_list.p;
-        a.cc_count = reinterpret_cast<unsigned int*>(ws.counters.p + 9);
+        a.cc_count = ws.counters.p + 9;
         a.cc_capacity = (int)std::min<size_t>(ws.cc_list.cap, (size_t)INT32_MAX);
         a.cc_half = ws.cc_half.p;
         a.skip_unflagged = 1;
@@ -828,7 +828,7 @@ lk_status lk_get_stats(lk_ctx* ctx, lk_stats* out) {
         ctx->stats.cc_candidates = 0;
         ctx->stats.cc_fallback_pairs = 0;
         if (ctx->stats_cc) {
-            ctx->stats.cc_candidates = u32[14];          // low half of counters[9]
+            ctx->stats.cc_candidates = (int64_t)(u32[14] | ((unsigned long long)u32[15] << 32));   // counters[9]
             std::vector<int> fl((size_t)std::max<int64_t>(ctx->stats_tasks, 1), 0);
             if (ctx->stats_tasks > 0)
                 LK_CUDA(ctx, cudaMemcpy(fl.data(), ctx->stats_flags, ctx->stats_tasks * sizeof(int),

@@ -114,7 +114,7 @@ struct SweepArgs {
     float near_ratio_sq;           // tau^2
     // Counting crossings (lk_options.method = LK_METHOD_CC).
     NearEntry* cc_list;            // candidate crossings (task, j, i) for the FP64 resolve
-    unsigned int* cc_count;        // [1] entries of cc_list (may exceed capacity)
+    unsigned long long* cc_count;  // [1] candidates found (may exceed the list's capacity)
     int cc_capacity;
     int* cc_half;                  // [n_tasks] twice the linking number by crossings
     int skip_unflagged;            // direct-sum sweeps: only items of pairs flagged kFlagCcFallback

@@ -138,6 +138,72 @@ def double_helix_ribbon(twists, n, R=4.0, w=0.3) -> Geometry:
     return from_loops(loops, name=f"ribbon_{twists}", pairs=[[0, 1]], meta={"abs_lk": twists})
 
 
+def _spherical_winding(nu, n, radius, tilt, R3) -> np.ndarray:
+    """One woundball curve: a great circle of the given radius, tilted by ``tilt``
+    off the polar axis so that it misses the poles, and turned one full
+    revolution about the polar axis over ``nu`` passes.  It passes near the
+    north pole ``nu`` times and closes after the last pass; the whole curve is
+    then rotated by ``R3``."""
+    t = np.arange(n) * (2.0 * np.pi * nu / n)
+    g = np.stack([np.sin(t), -np.cos(t) * np.sin(tilt), np.cos(t) * np.cos(tilt)], 1)
+    a = t / nu
+    c, s = np.cos(a), np.sin(a)
+    p = np.stack([c * g[:, 0] - s * g[:, 1], s * g[:, 0] + c * g[:, 1], g[:, 2]], 1)
+    return radius * p @ R3.T
+
+
+def woundball(nu, n, n2=None, R=1.0, ratio=0.5, seed=5) -> Geometry:
+    """The paper's woundball stress test (Fig. "Large-Input Stress Tests"): two
+    similar spherical curves on concentric spheres of radii R and ratio*R, each
+    passing near the north pole ``nu`` times.  The inner curve lies in a ball
+    that the outer sphere does not meet, so it can be shrunk to a point
+    without crossing the outer curve: lk = 0, reached by a sum of many terms
+    that cancel."""
+    rng = np.random.default_rng(seed)
+    a = _spherical_winding(nu, n, R, 0.05, np.eye(3))
+    b = _spherical_winding(nu, n if n2 is None else n2, ratio * R, 0.08, random_rotation(rng))
+    return from_loops([a, b], name=f"woundball_{nu}", pairs=[[0, 1]], meta={"abs_lk": 0})
+
+
+def _rectangle(corners, nseg) -> np.ndarray:
+    """Closed polyline through the four corners, ``nseg`` segments shared among
+    the sides in proportion to their lengths (every corner is a vertex)."""
+    corners = np.asarray(corners, np.float64)
+    side = np.linalg.norm(np.roll(corners, -1, 0) - corners, axis=1)
+    per = np.maximum(1, np.round(nseg * side / side.sum()).astype(int))
+    per[np.argmax(per)] += nseg - per.sum()
+    pts = []
+    for k in range(4):
+        u = np.arange(per[k])[:, None] / per[k]
+        pts.append(corners[k] + u * (corners[(k + 1) % 4] - corners[k]))
+    return np.concatenate(pts, 0)
+
+
+def square_links(n, nseg, w=0.25, gap=1.0, sigma=1e-3, seed=6, dtype=np.float64) -> Geometry:
+    """The paper's thick square link stress test (Fig. "Large-Input Stress
+    Tests"): L = 2n long flat rectangles, n in the planes y = a*gap and n in the
+    planes x = b*gap, woven so that every rectangle of one family threads every
+    rectangle of the other exactly once: L^2/4 linked pairs, each |lk| = 1,
+    all of one sign, and no linked pair within a family.  Rectangle a spans
+    z in [-w, w]; rectangle b spans z in [0, 2w], so only its lower long side
+    passes through rectangle a.  Loops are ordered a = 0..n-1, then b; the
+    closest approach of two loops is w.  Seeded jitter (sigma*w) keeps the
+    vertices in general position."""
+    rng = np.random.default_rng(seed)
+    lo, hi = -gap, n * gap
+    loops = []
+    for a in range(n):
+        y = a * gap
+        loops.append(_rectangle([[lo, y, -w], [hi, y, -w], [hi, y, w], [lo, y, w]], nseg))
+    for b in range(n):
+        x = b * gap + 0.5 * gap
+        loops.append(_rectangle([[x, lo, 0.0], [x, lo, 2 * w], [x, hi, 2 * w], [x, hi, 0.0]], nseg))
+    loops = [x + rng.normal(scale=sigma * w, size=x.shape) for x in loops]
+    aa, bb = np.meshgrid(np.arange(n), np.arange(n, 2 * n), indexing="ij")
+    pairs = np.stack([aa.ravel(), bb.ravel()], 1)
+    return from_loops(loops, dtype=dtype, name=f"square_links_{n}", pairs=pairs, meta={"abs_lk": 1})
+
+
 def whitehead(n1=200, n2=400, h=0.5, lift=0.3) -> Geometry:
     """Whitehead link as a reduced alternating 5-crossing diagram: loop 2 is a
     lemniscate (figure-eight) in the xy-plane whose self-crossing is lifted by

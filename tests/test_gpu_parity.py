@@ -247,6 +247,23 @@ def test_near_segments_take_the_fp64_path():
     assert st2[0] == 0 and lk2[0] == lk_o[0] and abs(raw2[0] - ref[0]) <= RAW_TOL
 
 
+@pytest.mark.parametrize("chunk_capacity", [1, 3, 8, 40, 1 << 20])
+def test_chunk_list_overflow_part_way_through_an_item(chunk_capacity):
+    """Square links put near segment pairs in two chunks of one work item (each
+    rectangle passes within w = L/2 of both long sides of the other, which lie
+    in the two halves of its 60 rows).  When the chunk list fills after some
+    of an item's chunks went to it, the item is swept again whole; its near
+    pairs must be counted once, in both paths."""
+    g = W.square_links(12, 60)
+    ref = O.link_pairs(g.vertices, g.offsets, g.pairs)
+    for near_capacity in (1 << 20, 7):
+        lk_o, raw, st, s = run(g, stats=True, chunk_capacity=chunk_capacity, near_capacity=near_capacity)
+        assert np.all(st == 0) and np.array_equal(lk_o, O.round_lk(ref).astype(np.int32))
+        assert np.max(np.abs(raw - ref)) <= RAW_TOL, (near_capacity, np.max(np.abs(raw - ref)))
+        assert s["careful_chunks"] > 0 and s["fp64_pairs"] > 0
+        assert (s["careful_items"] > 0) == (chunk_capacity <= 40)
+
+
 def threaded_ring(n_small, n_big, centre_row=16, r_small=0.1, seed=7):
     """A unit ring (n_big segments) threaded by a ring of radius r_small centred
     on its wire next to row segment centre_row, in the plane normal to the

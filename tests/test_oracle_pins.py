@@ -110,7 +110,8 @@ def pin_closed_forms(lib):
     bad = []
     for c in cases:
         g = getattr(W, c["fn"])(*c["args"])
-        raw = O.link(g.loop(0), g.loop(1), lib=lib)
+        a, b = c.get("pair", [0, 1])
+        raw = O.link(g.loop(a), g.loop(b), lib=lib)
         if abs(abs(raw) - c["abs_lk"]) > 1e-8:
             bad.append((c["name"], raw))
     return not bad, bad
@@ -139,10 +140,26 @@ def test_closed_forms_golden():
 def test_closed_form_signs_match_crossing_count():
     rng = np.random.default_rng(1)
     for g in [W.hopf(24, 30), W.torus_link(2, 3, 150), W.double_helix_ribbon(4, 160), W.torus_periods(2, 3, 90, 90),
-              W.whitehead(50, 70)]:
+              W.whitehead(50, 70), W.woundball(6, 300)]:
         cc = linking_number_exact(g.loop(0), g.loop(1), rng)
         raw = O.link(g.loop(0), g.loop(1))
         assert abs(raw - cc) < 1e-9, (g.name, raw, cc)
+
+
+def test_square_links_exactly_the_cross_family_pairs_link():
+    """Thick square links (Fig. "Large-Input Stress Tests"): every pair of
+    rectangles from different families links once, with one sign, and no two
+    of one family link; the exact crossing count fixes each value."""
+    rng = np.random.default_rng(2)
+    g = W.square_links(3, 40)
+    for a in range(g.n_loops):
+        for b in range(a + 1, g.n_loops):
+            cc = linking_number_exact(g.loop(a), g.loop(b), rng)
+            raw = O.link(g.loop(a), g.loop(b))
+            assert abs(raw - cc) < 1e-9, (a, b, raw, cc)
+            assert cc == (1 if (a < 3) != (b < 3) else 0), (a, b, cc)
+    # the boxes of one family are disjoint, so the box search keeps exactly the linked pairs
+    assert np.array_equal(W.aabb_candidates(g.vertices, g.offsets), g.pairs)
 
 
 def test_term_bounds_and_segment_reversal_antisymmetry():
