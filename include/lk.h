@@ -84,7 +84,12 @@ typedef struct lk_options {
     size_t mem_budget;   /* device bytes one verify may use for its work buffers, 0 = unlimited */
     int tile_rows;       /* rows per work item; 0 = chosen by the built-in tuner */
     int near_capacity;   /* entries of the FP64 recompute list (default 1<<20); overflow is
-                            evaluated in place, results are unchanged */
+                            evaluated in place, results are unchanged.  This and the two
+                            list sizes below are starting sizes: when a plain lk_verify
+                            overflowed a list, a later lk_verify on the context grows it
+                            to the next power of two above that call's need (at most 2^28
+                            entries; 2^26 for chunks) -- unless mem_budget is set.  The
+                            context then holds the grown size (lk_get_options shows it). */
     int timing;          /* 1: time the bulk sweep kernel with CUDA events on the launch stream
                             (read back by lk_get_stats as sweep_ms); default 0 */
     int chunk_capacity;  /* entries of the chunk hand-over list (default 1<<20); an overflow
@@ -204,6 +209,10 @@ lk_status lk_sync(lk_ctx* ctx, void* cuda_stream);
 
 /* Statistics of the most recent completed verify or plan run on this context. */
 lk_status lk_get_stats(lk_ctx* ctx, lk_stats* out);
+
+/* The options the context runs with: those given to lk_create, with the
+ * list sizes as grown by later verifies.  Errors: LK_ERR_ARG. */
+lk_status lk_get_options(const lk_ctx* ctx, lk_options* out);
 
 /* Free the context and its device memory.  NULL is ignored. */
 void lk_destroy(lk_ctx* ctx);

@@ -167,6 +167,14 @@ struct lk_ctx {
     int64_t* d_pls_offsets = nullptr;    // [n_loops]
     int32_t* d_pls_pairs = nullptr;      // staging for host destinations
     int64_t pls_pairs_cap = 0;
+    // List growth: after each lk_verify its work counters are copied to pinned
+    // host memory on the stream; a later lk_verify reads them once the copy has
+    // landed (without waiting for it) and enlarges any list that overflowed.
+    unsigned long long* h_counters = nullptr;   // [10], pinned
+    cudaEvent_t counters_ev = nullptr;
+    bool counters_pending = false;
+    int64_t counters_item_chunks = 0;           // that verify's chunks per work item (at most)
+    int64_t counters_chunks = 0;                // and its chunks in all
     std::string err;
 };
 
@@ -185,6 +193,75 @@ static void drop_repeat_plan(lk_ctx* ctx) {
     if (ctx->repeat_plan) lk_plan_destroy(ctx->repeat_plan);
     ctx->repeat_plan = nullptr;
     ctx->last_pairs.clear();
+}
+
+// Upper bounds of automatic list growth (entries): 4 GB of FP64 recompute
+// entries, 1 GB of chunk hand-overs, 4 GB of crossing candidates.
+constexpr int64_t kGrowNearMax = (int64_t)1 << 28;
+constexpr int64_t kGrowChunkMax = (int64_t)1 << 26;
+constexpr int64_t kGrowCcMax = (int64_t)1 << 28;
+
+// Enlarge the recompute, chunk and candidate lists to what the previous
+// lk_verify on this context asked for (the next power of two above it, within
+// the bounds above).  An overflow never changes a result -- the overflowing
+// entries are evaluated in place, handed over whole or decided by the direct
+// sum -- but each of those is slower than the list it replaces.  A context
+// with a memory budget keeps its configured sizes.
+static void grow_lists(lk_ctx* ctx) {
+    if (!ctx->counters_pending) return;
+    const cudaError_t q = cudaEventQuery(ctx->counters_ev);
+    if (q == cudaErrorNotReady) {
+        cudaGetLastError();        // not an error: the copy has not landed yet
+        return;
+    }
+    ctx->counters_pending = false;
+    if (q != cudaSuccess || ctx->opt.mem_budget > 0) return;
+    const unsigned long long* h = ctx->h_counters;
+    const unsigned long long need_near = h[3] & 0xffffffffull;     // near_count: low half of counters[3]
+    // chunk_count (low half of counters[5]) misses the chunks an item did not
+    // reach after its hand-over failed; each item handed over whole (careful
+    // count, low half of counters[2]) may have had all of its chunks to hand
+    const unsigned long long whole = h[2] & 0xffffffffull;
+    const unsigned long long need_chunk =
+        std::min<unsigned long long>((h[5] & 0xffffffffull) + whole * (unsigned long long)ctx->counters_item_chunks,
+                                     (unsigned long long)std::max<int64_t>(ctx->counters_chunks, 1));
+    const unsigned long long need_cc = h[9];                       // crossing candidates
+    auto grown = [](int cur, unsigned long long need, int64_t limit) {
+        if (need <= (unsigned long long)cur) return cur;
+        int64_t n = 1;
+        while ((unsigned long long)n < need && n < limit) n <<= 1;
+        return (int)std::max<int64_t>(cur, std::min<int64_t>(n, limit));
+    };
+    const int near = grown(ctx->opt.near_capacity, need_near, kGrowNearMax);
+    const int chunk = grown(ctx->opt.chunk_capacity, need_chunk, kGrowChunkMax);
+    const int cc = ctx->opt.method == LK_METHOD_CC ? grown(ctx->opt.cc_capacity, need_cc, kGrowCcMax)
+                                                   : ctx->opt.cc_capacity;
+    if (near == ctx->opt.near_capacity && chunk == ctx->opt.chunk_capacity && cc == ctx->opt.cc_capacity) return;
+    ctx->opt.near_capacity = near;
+    ctx->opt.chunk_capacity = chunk;
+    ctx->opt.cc_capacity = cc;
+    drop_repeat_plan(ctx);         // its work buffers have the old sizes
+}
+
+// Queue the copy of a verify's work counters for grow_lists.  While the
+// previous copy is still in flight this verify's counters are not copied (the
+// host never waits here); a copy that landed unread is replaced by this one.
+static void note_counters(lk_ctx* ctx, const unsigned long long* d_counters, int64_t item_chunks,
+                          int64_t chunks, cudaStream_t s) {
+    if (!ctx->h_counters || !ctx->counters_ev) return;
+    if (ctx->counters_pending && cudaEventQuery(ctx->counters_ev) == cudaErrorNotReady) {
+        cudaGetLastError();
+        return;
+    }
+    ctx->counters_pending = false;
+    ctx->counters_item_chunks = item_chunks;
+    ctx->counters_chunks = chunks;
+    if (cudaMemcpyAsync(ctx->h_counters, d_counters, 10 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) ==
+            cudaSuccess &&
+        cudaEventRecord(ctx->counters_ev, s) == cudaSuccess)
+        ctx->counters_pending = true;
+    else
+        cudaGetLastError();
 }
 
 namespace {
@@ -679,6 +756,8 @@ lk_status lk_create(lk_ctx** out, const void* vertices, lk_dtype vdtype, int64_t
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counters, 10 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->counters_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         const lk_status st = cuda_fail(nullptr, e, "lk_create");
         lk_destroy(ctx);
@@ -712,6 +791,12 @@ lk_status lk_update(lk_ctx* ctx, const void* data, lk_dtype dtype, int is_delta,
     return LK_OK;
 }
 
+lk_status lk_get_options(const lk_ctx* ctx, lk_options* out) {
+    if (!ctx || !out) return fail(nullptr, LK_ERR_ARG, "lk_get_options: NULL argument");
+    *out = ctx->opt;
+    return LK_OK;
+}
+
 lk_status lk_verify(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, int32_t* lk_out,
                     double* raw_out, int32_t* status_out, void* cuda_stream) {
     if (!ctx) return fail(nullptr, LK_ERR_ARG, "lk_verify: NULL context");
@@ -722,6 +807,7 @@ lk_status lk_verify(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, int
     std::vector<int32_t> hp;
     lk_status st = get_pairs_on_host(ctx, loop_pairs, n_pairs, s, hp);
     if (st != LK_OK) return st;
+    grow_lists(ctx);
     if (hp == ctx->last_pairs) {
         // the same list as the last call: replay its plan (built on the first repeat)
         if (!ctx->repeat_plan) {
@@ -729,7 +815,12 @@ lk_status lk_verify(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, int
             if ((st = lk_plan_create(ctx, hp.data(), n_pairs, &plan, cuda_stream)) != LK_OK) return st;
             ctx->repeat_plan = plan;
         }
-        return lk_plan_run(ctx->repeat_plan, lk_out, raw_out, status_out, cuda_stream);
+        st = lk_plan_run(ctx->repeat_plan, lk_out, raw_out, status_out, cuda_stream);
+        const Packed& rp = ctx->repeat_plan->pk;
+        if (st == LK_OK)
+            note_counters(ctx, ctx->repeat_plan->ws.counters.p,
+                          (rp.tile_rows_max + lk::kChunkRows - 1) / lk::kChunkRows, rp.n_chunks, s);
+        return st;
     }
     drop_repeat_plan(ctx);
     Packed pk;
@@ -739,7 +830,11 @@ lk_status lk_verify(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, int
     if ((st = enqueue_verify(ctx, ctx->ws, pk, s)) != LK_OK) return st;
     note_stats(ctx, ctx->ws, pk, s);
     ctx->last_pairs.swap(hp);
-    return copy_outputs(ctx, ctx->ws, n_pairs, lk_out, raw_out, status_out, s);
+    st = copy_outputs(ctx, ctx->ws, n_pairs, lk_out, raw_out, status_out, s);
+    if (st == LK_OK)
+        note_counters(ctx, ctx->ws.counters.p, (pk.tile_rows_max + lk::kChunkRows - 1) / lk::kChunkRows,
+                      pk.n_chunks, s);
+    return st;
 }
 
 lk_status lk_candidates(lk_ctx* ctx, int32_t* pairs_out, int64_t capacity, int64_t* n_pairs,
@@ -861,6 +956,11 @@ void lk_destroy(lk_ctx* ctx) {
     if (ctx->d_pls_offsets) cudaFree(ctx->d_pls_offsets);
     if (ctx->d_pls_pairs) cudaFree(ctx->d_pls_pairs);
     if (ctx->d_stage) cudaFree(ctx->d_stage);
+    if (ctx->counters_ev) {
+        cudaEventSynchronize(ctx->counters_ev);
+        cudaEventDestroy(ctx->counters_ev);
+    }
+    if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     delete ctx;
 }
 

@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "LK_OK", 1: "LK_ERR_ARG", 2: "LK_ERR_ZERO_SEGMENT", 3: "LK_ER
                 4: "LK_ERR_NONINTEGER", 5: "LK_ERR_OOM", 6: "LK_ERR_TIMEOUT", 7: "LK_ERR_CUDA",
                 8: "LK_ERR_BUSY"}
 
-EXPORTED = ["lk_default_options", "lk_create", "lk_update", "lk_verify", "lk_sync", "lk_get_stats",
+EXPORTED = ["lk_default_options", "lk_create", "lk_update", "lk_verify", "lk_sync", "lk_get_stats", "lk_get_options",
             "lk_destroy", "lk_last_error", "lk_plan_create", "lk_plan_run", "lk_plan_destroy",
             "lk_verify_noalloc", "lk_verify_expected", "lk_autotune", "lk_tune_get", "lk_tune_set", "lk_server_default_options", "lk_server_create", "lk_server_stream",
             "lk_server_submit", "lk_server_step", "lk_server_poll", "lk_server_completed",
@@ -111,6 +111,8 @@ def load(path: str | None = None):
     lib.lk_candidates.argtypes = [vp, vp, i64, ctypes.POINTER(i64), vp]
     lib.lk_get_stats.restype = ctypes.c_int
     lib.lk_get_stats.argtypes = [vp, ctypes.POINTER(lk_stats)]
+    lib.lk_get_options.restype = ctypes.c_int
+    lib.lk_get_options.argtypes = [vp, ctypes.POINTER(lk_options)]
     lib.lk_destroy.restype = None
     lib.lk_destroy.argtypes = [vp]
     lib.lk_last_error.restype = ctypes.c_char_p
@@ -259,6 +261,12 @@ def lk_get_stats(ctx) -> dict:
     s = lk_stats()
     _check(load().lk_get_stats(ctx, ctypes.byref(s)), ctx)
     return {k: getattr(s, k) for k, _ in lk_stats._fields_}
+
+
+def lk_get_options(ctx) -> lk_options:
+    o = lk_options()
+    _check(load().lk_get_options(ctx, ctypes.byref(o)), ctx)
+    return o
 
 
 def lk_destroy(ctx):

@@ -264,6 +264,48 @@ def test_chunk_list_overflow_part_way_through_an_item(chunk_capacity):
         assert (s["careful_items"] > 0) == (chunk_capacity <= 40)
 
 
+def test_overflowed_lists_grow_for_later_verifies():
+    """A verify that overflowed the recompute and chunk lists leaves its need on
+    the context; the next verify runs with lists that fit (and with a memory
+    budget the sizes stay as configured).  Every call matches the oracle."""
+    g = W.square_links(12, 60)
+    ref = O.link_pairs(g.vertices, g.offsets, g.pairs)
+    stream = torch.cuda.current_stream()
+    v = torch.from_numpy(g.vertices).cuda()
+    off = torch.from_numpy(g.offsets).cuda()
+    pr = torch.from_numpy(g.pairs).cuda()
+    n = g.pairs.shape[0]
+    for budget in (0, 1 << 40):
+        o = lk.lk_default_options()
+        o.near_capacity, o.chunk_capacity, o.mem_budget = 7, 1, budget
+        ctx = lk.lk_create(v, off, o, stream)
+        try:
+            runs = []
+            for _ in range(3):       # plain, grown plain, plan replay of the same list
+                lk_o = torch.zeros(n, dtype=torch.int32, device="cuda")
+                raw = torch.zeros(n, dtype=torch.float64, device="cuda")
+                st = torch.zeros(n, dtype=torch.int32, device="cuda")
+                lk.lk_verify(ctx, pr, lk_o, raw, st, stream)
+                torch.cuda.synchronize()
+                runs.append((lk_o.cpu().numpy(), raw.cpu().numpy(), st.cpu().numpy(), lk.lk_get_stats(ctx)))
+            grown = lk.lk_get_options(ctx)
+        finally:
+            lk.lk_destroy(ctx)
+        for lk_o, raw, st, _ in runs:
+            assert np.all(st == 0) and np.array_equal(lk_o, O.round_lk(ref).astype(np.int32))
+            assert np.max(np.abs(raw - ref)) <= RAW_TOL
+        first = runs[0][3]
+        assert first["near_overflow"] > 0 and first["careful_items"] > 0
+        if budget:
+            assert (grown.near_capacity, grown.chunk_capacity) == (7, 1)
+            assert runs[2][3]["near_overflow"] > 0
+        else:
+            assert grown.near_capacity >= first["fp64_pairs"] and grown.chunk_capacity > 1
+            for _, _, _, s in runs[1:]:
+                assert s["near_overflow"] == 0 and s["careful_items"] == 0
+            assert np.array_equal(runs[1][1], runs[2][1])      # replay of the grown plan: bit-identical
+
+
 def threaded_ring(n_small, n_big, centre_row=16, r_small=0.1, seed=7):
     """A unit ring (n_big segments) threaded by a ring of radius r_small centred
     on its wire next to row segment centre_row, in the plane normal to the
