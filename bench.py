@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=600)
     return ap.parse_args()
 
@@ -233,6 +234,65 @@ def counting_crossings_block(g, v, off, pairs_d, lk_ref, stream, flush, steps=20
             "fallback_pairs": stats["cc_fallback_pairs"],
             "lk_equal_direct_sum": bool(np.array_equal(lo_h, lk_ref)),
             "exact_integer_raw": bool(np.all(raw_h == lo_h)), "all_status_ok": bool(np.all(st_h == 0))}
+
+
+def stress_block(stream, warm=3, reps=3):
+    """The paper's large-input stress shapes (Sec. 4, Table 1): a woundball
+    (nu = 10^3, 10^6 segments in two loops, lk = 0) and the thick square links
+    (1,250 loops, 5x10^5 segments, 390,625 pairs of lk = 1 from the device's
+    potential link search), each verified by the direct sum and by counting
+    crossings.  Times are CUDA-event medians of `reps` verifies after `warm`
+    untimed ones (the first sizes the work lists; the third builds the graph
+    plan of the repeated list)."""
+    import torch
+    from paper_2106_12655_gb300 import lk
+    from paper_2106_12655_gb300 import workloads as W
+
+    out = {}
+    for name, make, expect in (("woundball_nu1000", lambda: W.woundball(1000, 500_000), 0),
+                               ("square_links_1250", lambda: W.square_links(625, 400), 1)):
+        g = make()
+        g.vertices = g.vertices.astype(np.float32)
+        v = torch.from_numpy(g.vertices).cuda()
+        off = torch.from_numpy(g.offsets).cuda()
+        rec = {"loops": g.n_loops, "segments": int(g.vertices.shape[0])}
+        for label, method in (("direct_sum", lk.LK_METHOD_DS), ("counting_crossings", lk.LK_METHOD_CC)):
+            o = lk.lk_default_options()
+            o.method = method
+            ctx = lk.lk_create(v, off, o, stream)
+            try:
+                pairs = lk.lk_candidates(ctx, stream=stream)
+                n = pairs.shape[0]
+                pd = torch.from_numpy(pairs).cuda()
+                lo = torch.zeros(n, dtype=torch.int32, device=v.device)
+                raw = torch.zeros(n, dtype=torch.float64, device=v.device)
+                st = torch.zeros(n, dtype=torch.int32, device=v.device)
+                ms = []
+                for k in range(warm + reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    lk.lk_verify(ctx, pd, lo, raw, st, stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if k >= warm:
+                        ms.append(e0.elapsed_time(e1))
+                stats = lk.lk_get_stats(ctx)
+                lo_h, raw_h, st_h = lo.cpu().numpy(), raw.cpu().numpy(), st.cpu().numpy()
+            finally:
+                lk.lk_destroy(ctx)
+            sps = g.segment_pairs(pairs)
+            med = statistics.median(ms)
+            r = {"value": sps / (med / 1e3), "unit": UNIT, "ms": med, "pairs": int(n), "segment_pairs": int(sps),
+                 "lk_all_expected": bool(np.all(lo_h == expect)), "all_status_ok": bool(np.all(st_h == 0)),
+                 "max_abs_raw_err": float(np.max(np.abs(raw_h - expect))),
+                 "fp64_recomputed_segment_pairs": stats["fp64_pairs"]}
+            if method == lk.LK_METHOD_CC:
+                r["candidates"] = stats["cc_candidates"]
+                r["fallback_pairs"] = stats["cc_fallback_pairs"]
+            rec[label] = r
+        out[name] = rec
+    return out
 
 
 def cpu_baseline(g):
@@ -440,6 +500,8 @@ def run_ours(args):
         line["counting_crossings"] = counting_crossings_block(g, v, off, pairs_d, lk_host, stream, flush)
     if not args.no_serving and world == 1:
         line["serving"] = serving_block(args)
+    if not args.no_stress and world == 1:
+        line["stress"] = stress_block(stream)
     if not args.no_cpu_baseline and world == 1:
         ref_raw, cb = cpu_baseline(g)
         line["cpu_baseline"] = cb
