@@ -35,6 +35,17 @@ def test_triangle_identity():
         assert abs(D * D + p * p - rhs) <= 1e-11 * rhs
 
 
+def test_edge_terms_from_distances():
+    """Law of cosines: for corners u, v joined by e = v - u,
+    2 H_uv = (|u| + |v|)^2 - |e|^2 (the fast sweep forms every edge term so)."""
+    rng = np.random.default_rng(4)
+    for _ in range(2000):
+        u, v = rng.normal(size=(2, 3)) * rng.uniform(0.1, 10, size=(2, 1))
+        lhs = 2 * H(u, v)
+        rhs = (np.linalg.norm(u) + np.linalg.norm(v)) ** 2 - np.linalg.norm(v - u) ** 2
+        assert abs(lhs - rhs) <= 1e-12 * (np.linalg.norm(u) + np.linalg.norm(v)) ** 2
+
+
 def test_parallelogram_cell_angle():
     rng = np.random.default_rng(2)
     checked = 0
