@@ -44,7 +44,7 @@ KERNELS_PER_STEP = 6
 # DRAM bytes (read + write) of one sweep_packed_kernel<fast> launch on this
 # workload, from one ncu capture of the current kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); set to None whenever the kernel changes.
-SWEEP_TRAFFIC_BYTES = 10003200
+SWEEP_TRAFFIC_BYTES = 10002688
 
 
 def parse():
