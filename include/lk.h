@@ -290,9 +290,14 @@ lk_status lk_tune_set(lk_ctx* ctx, const int32_t* entries, int64_t n_entries);
  * request with items left -- so a request that arrives while others run shares
  * the device with them.  A request's result does not depend on what shares
  * its waves (each pair's tiling and reduction order depend only on the pair).
- * All work of a server runs on its own stream (lk_server_stream); the caller
- * must not change (lk_update) a context while it has unfinished requests, or
- * must order the update on that stream after they finish.
+ * All work of a server runs on its own streams: request setup and the bulk
+ * waves on lk_server_stream, and each request's finishing passes (careful
+ * re-sweeps, FP64 recompute, reduction, result copies) on a second internal
+ * stream ordered after the request's last wave, so that the next wave
+ * overlaps them.  A request is complete (lk_server_poll, lk_server_completed)
+ * only when both are done.  The caller must not change (lk_update) a context
+ * while it has unfinished requests; an update enqueued on lk_server_stream
+ * after they are complete is ordered before every later wave.
  */
 typedef struct lk_server_options {
     int max_requests;     /* requests admitted at once (default 64) */

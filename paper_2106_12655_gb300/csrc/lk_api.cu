@@ -1279,7 +1279,8 @@ struct Request {
 };
 
 struct Wave {
-    cudaEvent_t done = nullptr;
+    cudaEvent_t done = nullptr;       // the wave and its requests' finishing work are done
+    cudaEvent_t swept = nullptr;      // the wave's bulk launches are done (finishing work waits for it)
     int slot = 0;
     std::vector<Request*> completing;
 };
@@ -1335,7 +1336,8 @@ struct lk_server {
     lk_server_options opt;
     int device = 0;
     int num_sms = 1;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;     // request setup and the bulk waves
+    cudaStream_t finish = nullptr;     // each finished request's careful passes, FP64 fix, reduction, copies
     unsigned char* d_arena = nullptr;
     unsigned char* h_arena = nullptr;
     Arena dev, host;
@@ -1420,6 +1422,7 @@ lk_status retire(lk_server* s, bool block) {
             s->st.completed += 1;
         }
         cudaEventDestroy(w.done);
+        if (w.swept) cudaEventDestroy(w.swept);
         s->slot_busy[w.slot] = false;
         s->waves.pop_front();
     }
@@ -1535,6 +1538,19 @@ lk_status launch_wave(lk_server* s) {
     lk::launch_wave(s->d_segs[slot], n_acc, acc_items, true, cnt, s->num_sms * lk::wave_blocks_per_sm(true), st);
     lk::launch_wave(s->d_segs[slot] + n_acc, n_fast, fast_items, false, cnt + 1,
                     s->num_sms * lk::wave_blocks_per_sm(false), st);
+    // The finishing work of the requests whose last items this wave holds runs
+    // on the second stream, after the wave: the next wave's bulk launches (on
+    // the first stream) overlap it instead of waiting behind these small,
+    // latency-bound kernels.  It touches only those requests' buffers.
+    Wave w;
+    w.slot = slot;
+    w.completing = completing;
+    if (!completing.empty()) {
+        LK_SRV_CUDA(s, cudaEventCreateWithFlags(&w.swept, cudaEventDisableTiming));
+        LK_SRV_CUDA(s, cudaEventRecord(w.swept, st));
+        LK_SRV_CUDA(s, cudaStreamWaitEvent(s->finish, w.swept, 0));
+        st = s->finish;
+    }
     for (Request* r : completing) {
         const bool fast = r->pk.n_items > r->pk.n_acc_items, acc = r->pk.n_acc_items > 0;
         lk::launch_careful_chunks(r->args, fast, acc, s->num_sms * lk::careful_chunk_blocks_per_sm(), st);
@@ -1561,9 +1577,6 @@ lk_status launch_wave(lk_server* s) {
                                        cudaMemcpyDeviceToHost, st));
     }
     LK_SRV_CUDA(s, cudaGetLastError());
-    Wave w;
-    w.slot = slot;
-    w.completing = completing;
     LK_SRV_CUDA(s, cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming));
     LK_SRV_CUDA(s, cudaEventRecord(w.done, st));
     s->slot_busy[slot] = true;
@@ -1602,6 +1615,7 @@ lk_status lk_server_create(lk_server** out, const lk_server_options* opt) {
     cudaGetDevice(&s->device);
     cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->finish, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_arena, o.arena_bytes);
     if (e == cudaSuccess) e = cudaHostAlloc(&s->h_arena, o.host_bytes, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_counters, 2 * kWaveSlots * sizeof(unsigned long long));
@@ -1725,7 +1739,11 @@ const char* lk_server_last_error(const lk_server* s) {
 void lk_server_destroy(lk_server* s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
-    for (Wave& w : s->waves) cudaEventDestroy(w.done);
+    if (s->finish) cudaStreamSynchronize(s->finish);
+    for (Wave& w : s->waves) {
+        cudaEventDestroy(w.done);
+        if (w.swept) cudaEventDestroy(w.swept);
+    }
     for (auto& kv : s->all) delete kv.second;
     for (int k = 0; k < kWaveSlots; ++k) {
         if (s->h_segs[k]) cudaFreeHost(s->h_segs[k]);
@@ -1735,6 +1753,7 @@ void lk_server_destroy(lk_server* s) {
     if (s->d_arena) cudaFree(s->d_arena);
     if (s->h_arena) cudaFreeHost(s->h_arena);
     if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->finish) cudaStreamDestroy(s->finish);
     delete s;
 }
 

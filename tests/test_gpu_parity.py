@@ -306,11 +306,11 @@ def test_overflowed_lists_grow_for_later_verifies():
             assert np.array_equal(runs[1][1], runs[2][1])      # replay of the grown plan: bit-identical
 
 
-def threaded_ring(n_small, n_big, centre_row=16, r_small=0.1, seed=7):
-    """A unit ring (n_big segments) threaded by a ring of radius r_small centred
-    on its wire next to row segment centre_row, in the plane normal to the
-    wire: linked (lambda = -1), every vertex-vertex distance about r_small, the
-    small ring's segments 2*pi*r_small/n_small long."""
+def threaded_ring(n_small, n_big, centre_row=16, r_small=0.1, seed=7, jitter=1e-4):
+    """A unit ring (n_big segments, seeded jitter) threaded by a ring of radius
+    r_small centred on its wire next to row segment centre_row, in the plane
+    normal to the wire: linked (lambda = -1), every vertex-vertex distance
+    about r_small, the small ring's segments 2*pi*r_small/n_small long."""
     rng = np.random.default_rng(seed)
     t = 2 * np.pi * np.arange(n_big) / n_big
     big = np.stack([np.cos(t), np.sin(t), np.zeros_like(t)], 1)
@@ -318,8 +318,23 @@ def threaded_ring(n_small, n_big, centre_row=16, r_small=0.1, seed=7):
     radial, up = np.array([np.cos(phi), np.sin(phi), 0.0]), np.array([0.0, 0.0, 1.0])
     u = 2 * np.pi * (np.arange(n_small) + 0.5) / n_small
     small = radial + r_small * (np.cos(u)[:, None] * radial + np.sin(u)[:, None] * up)
-    big += rng.normal(scale=1e-4, size=big.shape)
+    big += rng.normal(scale=jitter, size=big.shape)
     return W.from_loops([big, small], dtype=np.float64, pairs=[[0, 1]])
+
+
+@pytest.mark.parametrize("accurate_threshold", [0, 1 << 40])
+def test_far_cells_below_the_distance_floor(accurate_threshold):
+    """A ring of radius 5e-5 (64 segments) threading a unit ring of 640,000
+    segments: around it the cells are far in segment lengths (corners beyond
+    4.5 L) but closer than 1e-4 of the pair's frame, where the product of a
+    cell's four edge terms nears the FP32 underflow.  Those chunks must go to
+    the careful pass, in both arithmetic variants, and the pair must match the
+    oracle."""
+    g = threaded_ring(64, 640_000, centre_row=1000, r_small=5e-5, jitter=1e-7)
+    raw, ref = check_against_oracle(g, accurate_threshold=accurate_threshold)
+    assert ref[0] == pytest.approx(-1.0, abs=1e-9)
+    _, _, _, s = run(g, stats=True, accurate_threshold=accurate_threshold)
+    assert s["careful_chunks"] > 0
 
 
 @pytest.mark.parametrize("n_small,n_big,bulk", [(29, 314, True), (48, 512, True), (24, 400, False)])
