@@ -295,6 +295,61 @@ def stress_block(stream, warm=3, reps=3):
     return out
 
 
+def configs_block(stream, reps=3):
+    """The other workloads: the knit-yarn sheet (600 loops of 1k-20k segments,
+    all AABB candidates; every pair's distance from an integer -- its parity
+    against the oracle is a test) and the torus links (p,q) in {(2,3), (5,7),
+    (11,13), (31,37)} with 250k segments per component (error against the
+    closed form p*q).  Times are CUDA-event medians of `reps` verifies after
+    three untimed ones."""
+    import torch
+    from paper_2106_12655_gb300 import lk
+    from paper_2106_12655_gb300 import workloads as W
+
+    def timed(g):
+        v = torch.from_numpy(np.ascontiguousarray(g.vertices)).cuda()
+        off = torch.from_numpy(g.offsets).cuda()
+        ctx = lk.lk_create(v, off, None, stream)
+        try:
+            pd = torch.from_numpy(np.ascontiguousarray(g.pairs)).cuda()
+            n = g.pairs.shape[0]
+            lo = torch.zeros(n, dtype=torch.int32, device=v.device)
+            raw = torch.zeros(n, dtype=torch.float64, device=v.device)
+            st = torch.zeros(n, dtype=torch.int32, device=v.device)
+            ms = []
+            for k in range(3 + reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lk.lk_verify(ctx, pd, lo, raw, st, stream)
+                e1.record(stream)
+                e1.synchronize()
+                if k >= 3:
+                    ms.append(e0.elapsed_time(e1))
+            return statistics.median(ms), lo.cpu().numpy(), raw.cpu().numpy(), st.cpu().numpy()
+        finally:
+            lk.lk_destroy(ctx)
+
+    out = {}
+    g = W.knit_yarn()
+    med, lo, raw, st = timed(g)
+    sizes = g.sizes()[g.pairs].prod(axis=1)
+    out["knit_yarn"] = {"loops": g.n_loops, "pairs": int(g.pairs.shape[0]), "segment_pairs": int(sizes.sum()),
+                        "ms": med, "value": float(sizes.sum()) / (med / 1e3), "unit": UNIT,
+                        "all_status_ok": bool(np.all(st == 0)),
+                        "max_abs_raw_minus_lk": float(np.max(np.abs(raw - lo)))}
+    tl = []
+    for p, q in ((2, 3), (5, 7), (11, 13), (31, 37)):
+        g = W.torus_link(p, q, 250_000, dtype=np.float32)
+        med, lo, raw, st = timed(g)
+        sps = g.segment_pairs()
+        tl.append({"p": p, "q": q, "segments_per_component": 250_000, "ms": med, "value": sps / (med / 1e3),
+                   "unit": UNIT, "lk": int(lo[0]), "closed_form_abs_lk": p * q,
+                   "abs_raw_err_vs_closed_form": float(abs(abs(raw[0]) - p * q)), "status_ok": bool(st[0] == 0)})
+    out["torus_links"] = tl
+    return out
+
+
 def cpu_baseline(g):
     from oracle import oracle as O
 
@@ -502,6 +557,7 @@ def run_ours(args):
         line["serving"] = serving_block(args)
     if not args.no_stress and world == 1:
         line["stress"] = stress_block(stream)
+        line["configs"] = configs_block(stream)
     if not args.no_cpu_baseline and world == 1:
         ref_raw, cb = cpu_baseline(g)
         line["cpu_baseline"] = cb

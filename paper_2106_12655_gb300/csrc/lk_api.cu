@@ -141,6 +141,8 @@ struct lk_ctx {
     float4* d_R = nullptr;    // FP32 loop-relative copy of d_V (the mixed path reads it)
     int64_t* d_offsets = nullptr;
     double* d_aabb = nullptr;
+    unsigned long long* d_box_keys = nullptr;   // two sets of [6][n_loops] keys of the box passes
+    int box_set = 0;                            // the set in the reset state
     void* d_stage = nullptr;  // staging for host-side lk_update data
     size_t stage_bytes = 0;
     Workspace ws;
@@ -749,12 +751,14 @@ lk_status lk_create(lk_ctx** out, const void* vertices, lk_dtype vdtype, int64_t
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_offsets, off.size() * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_aabb, (size_t)n_loops * 6 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_R, (size_t)n_vertices * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_box_keys, (size_t)n_loops * 12 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_V, hv.data(), hv.size() * sizeof(Vtx), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_offsets, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) {
-        lk::launch_loop_aabb(ctx->d_V, ctx->d_offsets, n_loops, ctx->d_aabb, ctx->d_R, s);
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess) e = lk::reset_box_keys(ctx->d_box_keys, n_loops, s);
+    if (e == cudaSuccess)
+        e = lk::launch_loop_boxes(ctx->d_V, ctx->d_offsets, n_loops, n_vertices, ctx->d_box_keys,
+                                  ctx->d_box_keys + 6 * n_loops, ctx->d_aabb, ctx->d_R, nullptr, 0, 0, s);
+    ctx->box_set = 1;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counters, 10 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->counters_ev, cudaEventDisableTiming);
@@ -785,9 +789,11 @@ lk_status lk_update(lk_ctx* ctx, const void* data, lk_dtype dtype, int is_delta,
         LK_CUDA(ctx, cudaMemcpyAsync(ctx->d_stage, data, bytes, cudaMemcpyHostToDevice, s));
         src = ctx->d_stage;
     }
-    lk::launch_update(ctx->d_V, src, dtype == LK_F32 ? 0 : 1, is_delta ? 1 : 0, ctx->n_vertices, s);
-    lk::launch_loop_aabb(ctx->d_V, ctx->d_offsets, ctx->n_loops, ctx->d_aabb, ctx->d_R, s);
-    LK_CUDA(ctx, cudaGetLastError());
+    unsigned long long* cur = ctx->d_box_keys + 6 * ctx->n_loops * ctx->box_set;
+    unsigned long long* next = ctx->d_box_keys + 6 * ctx->n_loops * (1 - ctx->box_set);
+    LK_CUDA(ctx, lk::launch_loop_boxes(ctx->d_V, ctx->d_offsets, ctx->n_loops, ctx->n_vertices, cur, next,
+                                       ctx->d_aabb, ctx->d_R, src, dtype == LK_F32 ? 0 : 1, is_delta ? 1 : 0, s));
+    ctx->box_set = 1 - ctx->box_set;
     return LK_OK;
 }
 
@@ -950,6 +956,7 @@ void lk_destroy(lk_ctx* ctx) {
     if (ctx->d_V) cudaFree(ctx->d_V);
     if (ctx->d_offsets) cudaFree(ctx->d_offsets);
     if (ctx->d_aabb) cudaFree(ctx->d_aabb);
+    if (ctx->d_box_keys) cudaFree(ctx->d_box_keys);
     if (ctx->d_R) cudaFree(ctx->d_R);
     if (ctx->d_pls_keys) cudaFree(ctx->d_pls_keys);
     if (ctx->d_pls_counts) cudaFree(ctx->d_pls_counts);
@@ -1146,6 +1153,7 @@ extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, in
     double* raw_in = L.take<double>((size_t)kNoallocMaxVertices * 3);   // host vertices staged here
     ctx.d_offsets = L.take<int64_t>((size_t)kNoallocMaxLoops + 1);
     ctx.d_aabb = L.take<double>((size_t)kNoallocMaxLoops * 6);
+    ctx.d_box_keys = L.take<unsigned long long>((size_t)kNoallocMaxLoops * 12);
     Workspace ws;
     auto bind = [&](auto& buf, size_t count) {
         using T = typename std::remove_pointer<decltype(buf.p)>::type;
@@ -1176,9 +1184,9 @@ extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, in
                  (long long)pk.n_items, (long long)kNoallocMaxItems);
         return fail(nullptr, LK_ERR_ARG, msg);
     }
-    // Geometry into the scratch: the vertices as resident FP64 (the existing
-    // replace-vertices kernel converts from the caller's layout), offsets,
-    // loop boxes.
+    // Geometry into the scratch: offsets, then the vertices as resident FP64
+    // (the box passes replace them from the caller's layout) with the loop
+    // boxes and the FP32 loop-relative copy.
     const size_t vbytes = (size_t)n_vertices * 3 * (vdtype == LK_F32 ? 4 : 8);
     const void* vsrc = vertices;
     if (!is_device_ptr(vertices)) {
@@ -1189,8 +1197,12 @@ extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, in
     cudaError_t e = cudaMemcpyAsync(ctx.d_offsets, loop_offsets, (size_t)(n_loops + 1) * sizeof(int64_t),
                                     cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "lk_verify_noalloc: offsets");
-    lk::launch_update(ctx.d_V, vsrc, vdtype == LK_F32 ? 0 : 1, 0, n_vertices, s);
-    lk::launch_loop_aabb(ctx.d_V, ctx.d_offsets, n_loops, ctx.d_aabb, ctx.d_R, s);
+    e = lk::reset_box_keys(ctx.d_box_keys, n_loops, s);
+    if (e == cudaSuccess)
+        e = lk::launch_loop_boxes(ctx.d_V, ctx.d_offsets, n_loops, n_vertices, ctx.d_box_keys,
+                                  ctx.d_box_keys + 6 * n_loops, ctx.d_aabb, ctx.d_R, vsrc, vdtype == LK_F32 ? 0 : 1, 0,
+                                  s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "lk_verify_noalloc: geometry");
     if ((st = ensure_workspace(&ctx, ws, n_pairs, pk.n_items, pk.n_chunks)) != LK_OK ||
         (st = upload_packed(&ctx, ws, pk, s)) != LK_OK || (st = enqueue_verify(&ctx, ws, pk, s)) != LK_OK ||
         (st = copy_outputs(&ctx, ws, n_pairs, lk_out, raw_out, status_out, s)) != LK_OK)

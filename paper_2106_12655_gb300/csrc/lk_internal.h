@@ -143,8 +143,15 @@ struct ReduceArgs {
 };
 
 // Kernel launchers (lk_kernels.cu).
-void launch_loop_aabb(const Vtx* V, const int64_t* offsets, int64_t n_loops, double* aabb,
-                      float4* R, cudaStream_t s);
+// Loop boxes (FP64, [n_loops][6]) and the FP32 loop-relative copy R, after
+// applying `data` (if not null: [n_vertices][3] FP32 (dtype 0) or FP64, added
+// when is_delta, else replacing) to V.  keys and next_keys are two sets of
+// 6 * n_loops words: keys must be in the reset state (reset_box_keys, or a
+// previous call's next_keys); the call leaves next_keys reset for the next.
+cudaError_t reset_box_keys(unsigned long long* keys, int64_t n_loops, cudaStream_t s);
+cudaError_t launch_loop_boxes(Vtx* V, const int64_t* offsets, int64_t n_loops, int64_t n_vertices,
+                              unsigned long long* keys, unsigned long long* next_keys, double* aabb, float4* R,
+                              const void* data, int dtype, int is_delta, cudaStream_t s);
 void launch_pair_frames(PairTask* tasks, int64_t n_tasks, const double* aabb, cudaStream_t s);
 void launch_sweep_mixed(const SweepArgs& a, bool accurate, int64_t item_lo, int64_t item_hi,
                         unsigned long long* counter, int grid, cudaStream_t s);
@@ -159,7 +166,6 @@ void launch_wave(const WaveSeg* segs, int n_segs, int64_t n_items, bool accurate
                  unsigned long long* counter, int grid, cudaStream_t s);
 int wave_blocks_per_sm(bool accurate);
 void launch_reduce(const ReduceArgs& a, cudaStream_t s);
-void launch_update(Vtx* V, const void* data, int dtype, int is_delta, int64_t n, cudaStream_t s);
 int sweep_mixed_blocks_per_sm(bool accurate);
 
 // Counting crossings (lk_kernels.cu): the FP32 candidate sweep over all items

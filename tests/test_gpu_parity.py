@@ -457,6 +457,50 @@ def test_update_matches_fresh_context():
     assert np.abs(raw - ref).max() <= RAW_TOL
 
 
+def test_update_boxes_of_long_and_short_loops():
+    """Loop boxes are reduced over fixed vertex chunks: two torus-link
+    components of 60,001 and 50,003 vertices span hundreds of chunks, and 300
+    seven-vertex rings put many loops in one chunk.  After delta and absolute
+    updates (FP32 and FP64 data), the candidate pairs and every result must be
+    those of a fresh context built from the moved vertices."""
+    rng = np.random.default_rng(9)
+    tor = W.torus_link(5, 7, 60_001, n2=50_003)
+    small = [W.circle(rng.uniform(-3, 3, 3), np.array([1.0, 0, 0]), np.array([0, 1.0, 0]), 7, radius=0.2)
+             for _ in range(300)]
+    g = W.from_loops([tor.loop(0)] + small + [tor.loop(1)])
+    stream = torch.cuda.current_stream()
+    ctx = lk.lk_create(torch.from_numpy(g.vertices).cuda(), torch.from_numpy(g.offsets).cuda(), None, stream)
+    x = g.vertices.copy()
+    try:
+        for step in range(4):
+            if step % 2 == 0:
+                d = rng.normal(scale=1e-3, size=x.shape).astype(np.float32)
+                lk.lk_update(ctx, torch.from_numpy(d).cuda(), True, stream)
+                x = x + d.astype(np.float64)
+            else:
+                x = x + rng.normal(scale=1e-3, size=x.shape)
+                lk.lk_update(ctx, torch.from_numpy(x).cuda(), False, stream)
+            pairs = lk.lk_candidates(ctx, stream=stream)
+            n = pairs.shape[0]
+            out = np.zeros(n, np.int32), np.zeros(n), np.zeros(n, np.int32)
+            lk.lk_verify(ctx, pairs, *out, stream)
+            moved = W.Geometry(x.copy(), g.offsets, pairs)
+            fresh_ctx = lk.lk_create(torch.from_numpy(moved.vertices).cuda(), torch.from_numpy(g.offsets).cuda(),
+                                     None, stream)
+            try:
+                fresh_pairs = lk.lk_candidates(fresh_ctx, stream=stream)
+            finally:
+                lk.lk_destroy(fresh_ctx)
+            assert np.array_equal(pairs, fresh_pairs)
+            fresh = run(moved)
+            for a, b in zip(out, fresh):
+                assert np.array_equal(a, b)
+            k = pairs.tolist().index([0, 301])
+            assert out[2][k] == 0 and abs(out[0][k]) == 35
+    finally:
+        lk.lk_destroy(ctx)
+
+
 def test_autotune_changes_only_the_split(tmp_path):
     from paper_2106_12655_gb300 import tuning
 
