@@ -236,21 +236,26 @@ def counting_crossings_block(g, v, off, pairs_d, lk_ref, stream, flush, steps=20
             "exact_integer_raw": bool(np.all(raw_h == lo_h)), "all_status_ok": bool(np.all(st_h == 0))}
 
 
-def stress_block(stream, warm=3, reps=3):
+def stress_block(stream):
     """The paper's large-input stress shapes (Sec. 4, Table 1): a woundball
-    (nu = 10^3, 10^6 segments in two loops, lk = 0) and the thick square links
-    (1,250 loops, 5x10^5 segments, 390,625 pairs of lk = 1 from the device's
-    potential link search), each verified by the direct sum and by counting
-    crossings.  Times are CUDA-event medians of `reps` verifies after `warm`
-    untimed ones (the first sizes the work lists; the third builds the graph
-    plan of the repeated list)."""
+    (nu = 10^3, 10^6 segments in two loops, lk = 0) and the two thick square
+    links (1,250 loops, 5x10^5 segments, 390,625 pairs, and 5,000 loops,
+    4x10^6 segments, 6,250,000 pairs, all lk = 1, from the device's potential
+    link search), each verified by the direct sum and by counting crossings.
+    Times are CUDA-event medians of the timed verifies after untimed ones (for
+    the smaller shapes three: the first sizes the work lists, the third builds
+    the graph plan of the repeated list; the largest gets its lists sized up
+    front, one untimed and one timed verify)."""
     import torch
     from paper_2106_12655_gb300 import lk
     from paper_2106_12655_gb300 import workloads as W
 
     out = {}
-    for name, make, expect in (("woundball_nu1000", lambda: W.woundball(1000, 500_000), 0),
-                               ("square_links_1250", lambda: W.square_links(625, 400), 1)):
+    big = {"near_capacity": 1_400_000_000, "chunk_capacity": 1 << 26, "cc_capacity": 1 << 26}
+    for name, make, expect, opts, warm, reps in (
+            ("woundball_nu1000", lambda: W.woundball(1000, 500_000), 0, {}, 3, 3),
+            ("square_links_1250", lambda: W.square_links(625, 400), 1, {}, 3, 3),
+            ("square_links_5000", lambda: W.square_links(2500, 800), 1, big, 1, 1)):
         g = make()
         g.vertices = g.vertices.astype(np.float32)
         v = torch.from_numpy(g.vertices).cuda()
@@ -259,6 +264,8 @@ def stress_block(stream, warm=3, reps=3):
         for label, method in (("direct_sum", lk.LK_METHOD_DS), ("counting_crossings", lk.LK_METHOD_CC)):
             o = lk.lk_default_options()
             o.method = method
+            for k, val in opts.items():
+                setattr(o, k, val)
             ctx = lk.lk_create(v, off, o, stream)
             try:
                 pairs = lk.lk_candidates(ctx, stream=stream)

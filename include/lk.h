@@ -87,9 +87,10 @@ typedef struct lk_options {
                             evaluated in place, results are unchanged.  This and the two
                             list sizes below are starting sizes: when a plain lk_verify
                             overflowed a list, a later lk_verify on the context grows it
-                            to the next power of two above that call's need (at most 2^28
-                            entries; 2^26 for chunks) -- unless mem_budget is set.  The
-                            context then holds the grown size (lk_get_options shows it). */
+                            to the next power of two above that call's need (at most a
+                            quarter of the device memory then free, and 2^31 - 1 entries)
+                            -- unless mem_budget is set.  The context then holds the grown
+                            size (lk_get_options shows it). */
     int timing;          /* 1: time the bulk sweep kernel with CUDA events on the launch stream
                             (read back by lk_get_stats as sweep_ms); default 0 */
     int chunk_capacity;  /* entries of the chunk hand-over list (default 1<<20); an overflow

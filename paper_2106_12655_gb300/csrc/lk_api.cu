@@ -197,11 +197,16 @@ static void drop_repeat_plan(lk_ctx* ctx) {
     ctx->last_pairs.clear();
 }
 
-// Upper bounds of automatic list growth (entries): 4 GB of FP64 recompute
-// entries, 1 GB of chunk hand-overs, 4 GB of crossing candidates.
-constexpr int64_t kGrowNearMax = (int64_t)1 << 28;
-constexpr int64_t kGrowChunkMax = (int64_t)1 << 26;
-constexpr int64_t kGrowCcMax = (int64_t)1 << 28;
+// Upper bound of automatic list growth: a list grows to at most a quarter of
+// the device memory free at that moment (and 2^31 - 1 entries).
+static int64_t grow_limit(size_t entry_bytes) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return (int64_t)1 << 20;
+    }
+    return std::max<int64_t>(1, std::min<int64_t>(INT32_MAX, (int64_t)(free_b / 4 / entry_bytes)));
+}
 
 // Enlarge the recompute, chunk and candidate lists to what the previous
 // lk_verify on this context asked for (the next power of two above it, within
@@ -228,15 +233,16 @@ static void grow_lists(lk_ctx* ctx) {
         std::min<unsigned long long>((h[5] & 0xffffffffull) + whole * (unsigned long long)ctx->counters_item_chunks,
                                      (unsigned long long)std::max<int64_t>(ctx->counters_chunks, 1));
     const unsigned long long need_cc = h[9];                       // crossing candidates
-    auto grown = [](int cur, unsigned long long need, int64_t limit) {
+    auto grown = [](int cur, unsigned long long need, size_t entry_bytes) {
         if (need <= (unsigned long long)cur) return cur;
+        const int64_t limit = grow_limit(entry_bytes);
         int64_t n = 1;
         while ((unsigned long long)n < need && n < limit) n <<= 1;
         return (int)std::max<int64_t>(cur, std::min<int64_t>(n, limit));
     };
-    const int near = grown(ctx->opt.near_capacity, need_near, kGrowNearMax);
-    const int chunk = grown(ctx->opt.chunk_capacity, need_chunk, kGrowChunkMax);
-    const int cc = ctx->opt.method == LK_METHOD_CC ? grown(ctx->opt.cc_capacity, need_cc, kGrowCcMax)
+    const int near = grown(ctx->opt.near_capacity, need_near, sizeof(NearEntry));
+    const int chunk = grown(ctx->opt.chunk_capacity, need_chunk, sizeof(lk::CarefulChunk));
+    const int cc = ctx->opt.method == LK_METHOD_CC ? grown(ctx->opt.cc_capacity, need_cc, sizeof(NearEntry))
                                                    : ctx->opt.cc_capacity;
     if (near == ctx->opt.near_capacity && chunk == ctx->opt.chunk_capacity && cc == ctx->opt.cc_capacity) return;
     ctx->opt.near_capacity = near;

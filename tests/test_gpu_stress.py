@@ -124,3 +124,24 @@ def test_square_links_paper_size(method):
         assert st["cc_fallback_pairs"] == 0 and np.array_equal(raw, lk_o.astype(np.float64))
     else:
         assert np.max(np.abs(raw - 1.0)) <= 1e-5, np.max(np.abs(raw - 1.0))
+
+
+@pytest.mark.parametrize("method", ["ds", "cc"])
+def test_square_links_paper_largest(method):
+    """Table 1's larger thick square link: 5,000 loops, 4x10^6 segments,
+    6,250,000 linked pairs (4x10^12 segment pairs, about 1e9 of them near
+    enough for the FP64 path), every one lk = 1; the work lists are sized for
+    it up front."""
+    g = W.square_links(2500, 800, dtype=np.float32)
+    assert g.vertices.shape[0] == 4_000_000
+    opts = ({"cc_capacity": 1 << 26} if method == "cc"
+            else {"near_capacity": 1_400_000_000, "chunk_capacity": 1 << 26})
+    pairs, lk_o, raw, status, st, dt = run(g, method=method, candidates=True, **opts)
+    print(f"square links 5000 {method}: {pairs.shape[0]} pairs in {dt:.2f} s; fp64 pairs {st['fp64_pairs']}, "
+          f"near overflow {st['near_overflow']}, candidates {st['cc_candidates']}")
+    assert np.array_equal(pairs, g.pairs)
+    assert np.all(status == lk.LK_OK) and np.all(lk_o == 1)
+    if method == "cc":
+        assert st["cc_fallback_pairs"] == 0 and np.array_equal(raw, lk_o.astype(np.float64))
+    else:
+        assert st["near_overflow"] == 0 and np.max(np.abs(raw - 1.0)) <= 1e-5
