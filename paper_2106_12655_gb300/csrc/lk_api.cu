@@ -73,8 +73,20 @@ struct DevBuf {
     size_t bytes_for(size_t n) const { return std::max<size_t>(n, 1) * sizeof(T); }
 };
 
+// A counting-crossings pair searched with the binned candidate search.
+struct GridJob {
+    int32_t task, n_rows, n_cols, G_max;   // G_max: the largest grid the pair may take
+};
+
+// Pairs with at least this many segment pairs take the binned candidate
+// search under LK_METHOD_CC (about the size at which its fixed launches cost
+// less than sweeping every segment pair).
+constexpr int64_t kCcGridMin = (int64_t)1 << 28;
+
 struct Packed {
     std::vector<PairTask> tasks;
+    std::vector<GridJob> grid;          // counting crossings: pairs for the binned search
+    int64_t grid_cells = 0, grid_rows = 0, grid_cols = 0;   // their largest sizes
     std::vector<int64_t> item_begin;
     std::vector<int32_t> item_task;
     int64_t n_items = 0;
@@ -105,6 +117,10 @@ struct Workspace {
                                           // [9] u32 crossing candidates
     DevBuf<NearEntry> cc_list;            // counting crossings: candidates (method CC only)
     DevBuf<int> cc_half;
+    DevBuf<unsigned int> grid_offsets, grid_cursor, grid_sums;   // binned search (largest grid pair)
+    DevBuf<int32_t> grid_entries;
+    DevBuf<float2> grid_row_xy, grid_col_xy;
+    DevBuf<unsigned long long> grid_meta;   // [0] entries total, [1] low half: the chosen grid size
     DevBuf<int32_t> lk;
     DevBuf<double> raw;
     DevBuf<int32_t> status;
@@ -125,6 +141,8 @@ struct Workspace {
         careful_items.release(); careful_chunks.release(); item_fix.release(); near_list.release(); fix_acc.release(); fp64_count.release();
         flags.release(); counters.release(); lk.release(); raw.release(); status.release();
         cc_list.release(); cc_half.release();
+        grid_offsets.release(); grid_cursor.release(); grid_sums.release(); grid_entries.release();
+        grid_row_xy.release(); grid_col_xy.release(); grid_meta.release();
     }
 };
 
@@ -405,6 +423,18 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
             t.tile_rows = q.tile_rows;
             t.col_tiles = q.col_tiles;
             t.accurate = q.accurate;
+            if (ctx->opt.method == LK_METHOD_CC && (int64_t)q.n_rows * q.n_cols >= kCcGridMin) {
+                // at most about 2 sqrt(N) cells per side; the device takes fewer
+                // where the segments are long (cells about 1.5 segment lengths)
+                const int64_t want = 2 * (int64_t)std::ceil(std::sqrt((double)std::max(q.n_rows, q.n_cols)));
+                int G = 64;
+                while (G < want && G < 4096) G <<= 1;
+                t.cc_grid = 1;
+                pk.grid.push_back(GridJob{(int32_t)k, q.n_rows, q.n_cols, G});
+                pk.grid_cells = std::max<int64_t>(pk.grid_cells, (int64_t)G * G);
+                pk.grid_rows = std::max<int64_t>(pk.grid_rows, q.n_rows);
+                pk.grid_cols = std::max<int64_t>(pk.grid_cols, q.n_cols);
+            }
             const int64_t full = q.n_rows / q.tile_rows, last = q.n_rows - full * q.tile_rows;
             const int64_t chunks_per_col = full * ((q.tile_rows + lk::kChunkRows - 1) / lk::kChunkRows) +
                                            (last > 0 ? (last + lk::kChunkRows - 1) / lk::kChunkRows : 0);
@@ -426,12 +456,26 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
 
 size_t chunk_capacity(const lk_options& o, int64_t n_chunks);
 
-size_t workspace_bytes(const lk_ctx* ctx, int64_t n_tasks, int64_t n_items, int64_t n_chunks) {
+// Row-segment entries of the binned search: with cells about 1.5 mean segment
+// lengths wide a row segment covers about two cells; a pair whose entries do
+// not fit goes to the direct sum.
+int64_t grid_entry_capacity(const Packed* pk) {
+    return pk && !pk->grid.empty() ? std::max<int64_t>(8 * pk->grid_rows, (int64_t)1 << 20) : 0;
+}
+
+size_t grid_bytes(const Packed* pk) {
+    if (!pk || pk->grid.empty()) return 0;
+    return (size_t)(2 * pk->grid_cells + 1 + pk->grid_cells / 4096 + 2) * sizeof(unsigned int) +
+           (size_t)grid_entry_capacity(pk) * sizeof(int32_t) + (size_t)(pk->grid_rows + pk->grid_cols) * sizeof(float2) +
+           2 * sizeof(unsigned long long);
+}
+
+size_t workspace_bytes(const lk_ctx* ctx, int64_t n_tasks, int64_t n_items, int64_t n_chunks, const Packed* pk) {
     const size_t near = (size_t)std::max(0, ctx->opt.near_capacity);
     const size_t cc = ctx->opt.method == LK_METHOD_CC ? (size_t)std::max(1, ctx->opt.cc_capacity) : 0;
     return n_tasks * (sizeof(PairTask) + 8 + 8 + 8 + 4 + 4 + 8 + 4 + (cc ? 4 : 0)) + n_items * (4 + 8 + 8 + 8) +
            chunk_capacity(ctx->opt, n_chunks) * sizeof(lk::CarefulChunk) +
-           (near + cc) * sizeof(NearEntry) + 80;
+           (near + cc) * sizeof(NearEntry) + grid_bytes(pk) + 80;
 }
 
 // Entries of the chunk hand-over list: every chunk of the batch, at most the
@@ -441,8 +485,9 @@ size_t chunk_capacity(const lk_options& o, int64_t n_chunks) {
     return (size_t)std::max<int64_t>(1, std::min<int64_t>(n_chunks, cap));
 }
 
-lk_status ensure_workspace(lk_ctx* ctx, Workspace& ws, int64_t n_tasks, int64_t n_items, int64_t n_chunks) {
-    if (ctx->opt.mem_budget > 0 && workspace_bytes(ctx, n_tasks, n_items, n_chunks) > ctx->opt.mem_budget)
+lk_status ensure_workspace(lk_ctx* ctx, Workspace& ws, int64_t n_tasks, int64_t n_items, int64_t n_chunks,
+                           const Packed* pk = nullptr) {
+    if (ctx->opt.mem_budget > 0 && workspace_bytes(ctx, n_tasks, n_items, n_chunks, pk) > ctx->opt.mem_budget)
         return fail(ctx, LK_ERR_OOM, "lk_verify: work buffers exceed mem_budget");
     const size_t nt = (size_t)std::max<int64_t>(n_tasks, 1), ni = (size_t)std::max<int64_t>(n_items, 1);
     LK_CUDA(ctx, ws.tasks.ensure(nt));
@@ -460,6 +505,15 @@ lk_status ensure_workspace(lk_ctx* ctx, Workspace& ws, int64_t n_tasks, int64_t 
     if (ctx->opt.method == LK_METHOD_CC) {
         LK_CUDA(ctx, ws.cc_list.ensure((size_t)std::max(1, ctx->opt.cc_capacity)));
         LK_CUDA(ctx, ws.cc_half.ensure(nt));
+        if (pk && !pk->grid.empty()) {
+            LK_CUDA(ctx, ws.grid_offsets.ensure((size_t)pk->grid_cells + 1));
+            LK_CUDA(ctx, ws.grid_cursor.ensure((size_t)pk->grid_cells));
+            LK_CUDA(ctx, ws.grid_sums.ensure((size_t)(pk->grid_cells / 4096 + 2)));
+            LK_CUDA(ctx, ws.grid_entries.ensure((size_t)grid_entry_capacity(pk)));
+            LK_CUDA(ctx, ws.grid_row_xy.ensure((size_t)pk->grid_rows));
+            LK_CUDA(ctx, ws.grid_col_xy.ensure((size_t)pk->grid_cols));
+            LK_CUDA(ctx, ws.grid_meta.ensure(2));
+        }
     }
     LK_CUDA(ctx, ws.lk.ensure(nt));
     LK_CUDA(ctx, ws.raw.ensure(nt));
@@ -553,6 +607,14 @@ lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStrea
                 // counting crossings first; the direct sum then runs only on the
                 // pairs it flagged (its sweeps skip every other item)
                 lk::launch_cc_sweep(a, ws.counters.p + 8, ctx->num_sms * lk::cc_sweep_blocks_per_sm(), s);
+                if (!pk.grid.empty()) {
+                    const lk::CcGridWork w{ws.grid_offsets.p, ws.grid_cursor.p, ws.grid_sums.p, ws.grid_entries.p,
+                                           (int64_t)std::min<size_t>(ws.grid_entries.cap, (size_t)INT32_MAX),
+                                           ws.grid_row_xy.p, ws.grid_col_xy.p,
+                                           reinterpret_cast<int*>(ws.grid_meta.p + 1), ws.grid_meta.p};
+                    for (const GridJob& gj : pk.grid)
+                        lk::launch_cc_grid(a, gj.task, gj.n_rows, gj.n_cols, gj.G_max, w, s);
+                }
                 lk::launch_cc_resolve(a, ctx->num_sms * 4, s);
             }
             lk::launch_sweep_mixed(a, true, 0, pk.n_acc_items, ws.counters.p + 0,
@@ -837,7 +899,7 @@ lk_status lk_verify(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, int
     drop_repeat_plan(ctx);
     Packed pk;
     if ((st = pack_pairs(ctx, hp.data(), n_pairs, pk)) != LK_OK) return st;
-    if ((st = ensure_workspace(ctx, ctx->ws, n_pairs, pk.n_items, pk.n_chunks)) != LK_OK) return st;
+    if ((st = ensure_workspace(ctx, ctx->ws, n_pairs, pk.n_items, pk.n_chunks, &pk)) != LK_OK) return st;
     if ((st = upload_packed(ctx, ctx->ws, pk, s)) != LK_OK) return st;
     if ((st = enqueue_verify(ctx, ctx->ws, pk, s)) != LK_OK) return st;
     note_stats(ctx, ctx->ws, pk, s);
@@ -991,7 +1053,7 @@ lk_status lk_plan_create(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs
     lk_plan* plan = new lk_plan();
     plan->ctx = ctx;
     if ((st = pack_pairs(ctx, hp.data(), n_pairs, plan->pk)) != LK_OK ||
-        (st = ensure_workspace(ctx, plan->ws, n_pairs, plan->pk.n_items, plan->pk.n_chunks)) != LK_OK ||
+        (st = ensure_workspace(ctx, plan->ws, n_pairs, plan->pk.n_items, plan->pk.n_chunks, &plan->pk)) != LK_OK ||
         (st = upload_packed(ctx, plan->ws, plan->pk, s)) != LK_OK) {
         lk_plan_destroy(plan);
         return st;
@@ -1803,7 +1865,7 @@ lk_status time_verify(lk_ctx* ctx, const std::vector<int32_t>& pairs, int tile_r
     lk_status st = pack_pairs(ctx, pairs.data(), (int64_t)(pairs.size() / 2), pk);
     ctx->opt.tile_rows = saved;
     if (st != LK_OK) return st;
-    if ((st = ensure_workspace(ctx, ctx->ws, (int64_t)pk.tasks.size(), pk.n_items, pk.n_chunks)) != LK_OK) return st;
+    if ((st = ensure_workspace(ctx, ctx->ws, (int64_t)pk.tasks.size(), pk.n_items, pk.n_chunks, &pk)) != LK_OK) return st;
     if ((st = upload_packed(ctx, ctx->ws, pk, s)) != LK_OK) return st;
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
@@ -1945,7 +2007,7 @@ extern "C" lk_status lk_verify_expected(lk_ctx* ctx, const int32_t* loop_pairs, 
         const int64_t m = b1 - b0;
         Packed pk;
         if ((st = pack_pairs(ctx, hp.data() + 2 * b0, m, pk)) != LK_OK) return st;
-        if ((st = ensure_workspace(ctx, ctx->ws, m, pk.n_items, pk.n_chunks)) != LK_OK) return st;
+        if ((st = ensure_workspace(ctx, ctx->ws, m, pk.n_items, pk.n_chunks, &pk)) != LK_OK) return st;
         if ((st = upload_packed(ctx, ctx->ws, pk, s)) != LK_OK) return st;
         if ((st = enqueue_verify(ctx, ctx->ws, pk, s)) != LK_OK) return st;
         note_stats(ctx, ctx->ws, pk, s);

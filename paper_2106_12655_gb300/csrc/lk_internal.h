@@ -65,7 +65,7 @@ struct PairTask {
     int32_t out_index;   // position of the pair in the caller's list
     int32_t status;      // LK_OK, or LK_ERR_ARG for an invalid pair (then it has no items)
     int32_t accurate;    // 1: bias-free FP32 arithmetic variant (large pairs)
-    int32_t pad;
+    int32_t cc_grid;     // counting crossings: 1 when the pair's candidates come from the binned search
     float row_off[4];    // frame offset of the row loop's vertices ([3] unused)
     float col_off[4];    // frame offset of the column loop's vertices ([3] unused)
     float scale;         // power of two
@@ -171,6 +171,22 @@ int sweep_mixed_blocks_per_sm(bool accurate);
 // Counting crossings (lk_kernels.cu): the FP32 candidate sweep over all items
 // and the FP64 resolve of the candidates.
 void launch_cc_sweep(const SweepArgs& a, unsigned long long* counter, int grid, cudaStream_t s);
+// Binned candidate search of one counting-crossings pair (the pairs with
+// cc_grid set): a G x G grid over the pair's mapped frame.
+struct CcGridWork {
+    unsigned int* offsets;     // [G*G + 1]: cell counts, then their exclusive scan (total last)
+    unsigned int* cursor;      // [G*G]: fill positions
+    unsigned int* block_sums;  // [G*G / 4096 + 2]: scan scratch
+    int32_t* entries;          // [capacity]: row segments grouped by cell
+    int64_t capacity;
+    float2* row_xy;            // [n_rows]: mapped (x, y) of the row loop's vertices
+    float2* col_xy;            // [n_cols]
+    int* G;                    // [1]: the pair's grid size, chosen on the device
+    unsigned long long* total; // [1]: the pair's entries, counted in 64 bits
+};
+// G_max: the allocated grid size (offsets hold G_max^2 + 1 counts).
+void launch_cc_grid(const SweepArgs& a, int task, int n_rows, int n_cols, int G_max, const CcGridWork& w,
+                    cudaStream_t s);
 void launch_cc_resolve(const SweepArgs& a, int grid, cudaStream_t s);
 int cc_sweep_blocks_per_sm();
 

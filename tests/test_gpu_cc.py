@@ -126,3 +126,19 @@ def test_cc_reports_intersections():
     lk_o, raw, status, st = run_cc(g)
     assert status[0] == lk.LK_ERR_INTERSECT and lk_o[0] == 0
     assert status[1] == lk.LK_OK and lk_o[1] == 0 and raw[1] == 0.0
+
+
+@pytest.mark.parametrize("name", ["woundball", "torus", "ribbon", "whitehead"])
+def test_cc_binned_search_matches_oracle(name):
+    """Pairs of at least 2^28 segment pairs take the binned candidate search
+    (Algorithm 4's accelerated query, as a uniform grid over the projection):
+    the linking numbers must equal the oracle's, decided by crossings alone
+    (raw exact, no fallback)."""
+    g = {"woundball": lambda: W.woundball(100, 20_000),
+         "torus": lambda: W.torus_link(5, 7, 20_000, n2=17_001),
+         "ribbon": lambda: W.double_helix_ribbon(25, 20_000),
+         "whitehead": lambda: W.whitehead(20_000, 30_000)}[name]()
+    assert g.segment_pairs() >= 1 << 28
+    lk_o, raw, st = check(g)
+    assert st["cc_fallback_pairs"] == 0
+    assert np.array_equal(raw, lk_o.astype(np.float64))
