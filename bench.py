@@ -193,11 +193,12 @@ def pls_block(scenes):
     return out
 
 
-def counting_crossings_block(g, v, off, pairs_d, lk_ref, stream, flush, steps=20):
+def counting_crossings_block(g, v, off, pairs_d, lk_ref, stream, flush, steps=20, search=None):
     """The counting-crossings method (LK_METHOD_CC) on the same sheet and graph
     protocol: device time per step, and whether its linking numbers equal the
     direct sum's.  Its results are exact integers where the crossings decide a
-    pair."""
+    pair.  ``search`` picks the candidate search (default: the built-in choice,
+    here the one-CTA binned search for every pair)."""
     import torch
     from paper_2106_12655_gb300 import lk
 
@@ -205,6 +206,8 @@ def counting_crossings_block(g, v, off, pairs_d, lk_ref, stream, flush, steps=20
     o = lk.lk_default_options()
     o.method = lk.LK_METHOD_CC
     o.timing = 1
+    if search is not None:
+        o.cc_search = search
     ctx = lk.lk_create(v, off, o, stream)
     plan = lk.lk_plan_create(ctx, pairs_d, stream)
     lo = torch.zeros(n, dtype=torch.int32, device=v.device)
@@ -242,10 +245,10 @@ def stress_block(stream):
     links (1,250 loops, 5x10^5 segments, 390,625 pairs, and 5,000 loops,
     4x10^6 segments, 6,250,000 pairs, all lk = 1, from the device's potential
     link search), each verified by the direct sum and by counting crossings.
-    Times are CUDA-event medians of the timed verifies after untimed ones (for
-    the smaller shapes three: the first sizes the work lists, the third builds
-    the graph plan of the repeated list; the largest gets its lists sized up
-    front, one untimed and one timed verify)."""
+    Times are CUDA-event medians of the timed verifies after three untimed
+    ones (the first sizes the work lists -- the largest shape gets them sized
+    up front --, the third builds the graph plan of the repeated list, so the
+    timed verifies run that plan); the largest shape is timed once."""
     import torch
     from paper_2106_12655_gb300 import lk
     from paper_2106_12655_gb300 import workloads as W
@@ -560,6 +563,8 @@ def run_ours(args):
     }
     if world == 1:
         line["counting_crossings"] = counting_crossings_block(g, v, off, pairs_d, lk_host, stream, flush)
+        line["counting_crossings_all_pairs_sweep"] = counting_crossings_block(
+            g, v, off, pairs_d, lk_host, stream, flush, search=lk.LK_CC_SEARCH_SWEEP)
     if not args.no_serving and world == 1:
         line["serving"] = serving_block(args)
     if not args.no_stress and world == 1:

@@ -75,6 +75,17 @@ typedef enum {
     LK_METHOD_CC = 1
 } lk_method;
 
+/* How LK_METHOD_CC finds its candidate crossings (Algorithm 4 queries a
+ * hierarchy of one loop's projected segments with the other's).  Every
+ * choice returns the same results; they differ only in speed. */
+typedef enum lk_cc_search {
+    LK_CC_SEARCH_AUTO = 0,    /* binned where it pays: pairs whose loops both have at most 2,048
+                                 segments in one CTA each, pairs of at least 2^28 segment pairs
+                                 on a device-wide grid, the rest by the all-pairs sweep */
+    LK_CC_SEARCH_SWEEP = 1,   /* every pair by the all-pairs FP32 sweep */
+    LK_CC_SEARCH_BINNED = 2   /* every pair binned: one CTA where both loops fit, else the grid */
+} lk_cc_search;
+
 typedef struct lk_options {
     int precision;       /* lk_precision, default LK_MIXED */
     double near_ratio;   /* tau >= 3: a segment pair whose nearest corner distance (the smallest
@@ -106,6 +117,7 @@ typedef struct lk_options {
     int method;          /* lk_method, default LK_METHOD_DS */
     int cc_capacity;     /* LK_METHOD_CC: candidate crossings per verify (default 1<<18); pairs
                             whose candidates do not fit are computed by the direct sum */
+    int cc_search;       /* lk_cc_search, default LK_CC_SEARCH_AUTO */
 } lk_options;
 
 typedef struct lk_stats {

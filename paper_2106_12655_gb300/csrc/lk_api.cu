@@ -87,10 +87,13 @@ struct Packed {
     std::vector<PairTask> tasks;
     std::vector<GridJob> grid;          // counting crossings: pairs for the binned search
     int64_t grid_cells = 0, grid_rows = 0, grid_cols = 0;   // their largest sizes
+    int64_t n_cc_local = 0, n_cc_sweep = 0;   // counting crossings: one-CTA pairs, swept pairs
+    int32_t local_rows = 0, local_cols = 0;   // the one-CTA pairs' largest loops
     std::vector<int64_t> item_begin;
     std::vector<int32_t> item_task;
     int64_t n_items = 0;
     int64_t n_acc_items = 0;   // items [0, n_acc_items) belong to accurate-variant pairs
+    int64_t n_acc_tasks = 0;   // and tasks [0, n_acc_tasks)
     int64_t n_chunks = 0;      // 32-row chunks over all items
     int64_t segment_pairs = 0;
     int tile_rows_max = 0;
@@ -117,6 +120,7 @@ struct Workspace {
                                           // [9] u32 crossing candidates
     DevBuf<NearEntry> cc_list;            // counting crossings: candidates (method CC only)
     DevBuf<int> cc_half;
+    DevBuf<unsigned int> flag_scan, flag_sums;   // counting crossings: items of the undecided pairs
     DevBuf<unsigned int> grid_offsets, grid_cursor, grid_sums;   // binned search (largest grid pair)
     DevBuf<int32_t> grid_entries;
     DevBuf<float2> grid_row_xy, grid_col_xy;
@@ -140,7 +144,7 @@ struct Workspace {
         tasks.release(); item_begin.release(); item_task.release(); partial.release();
         careful_items.release(); careful_chunks.release(); item_fix.release(); near_list.release(); fix_acc.release(); fp64_count.release();
         flags.release(); counters.release(); lk.release(); raw.release(); status.release();
-        cc_list.release(); cc_half.release();
+        cc_list.release(); cc_half.release(); flag_scan.release(); flag_sums.release();
         grid_offsets.release(); grid_cursor.release(); grid_sums.release(); grid_entries.release();
         grid_row_xy.release(); grid_col_xy.release(); grid_meta.release();
     }
@@ -343,6 +347,10 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
     pk.tile_cols = tile_cols;
     pk.tile_rows_max = 0;
     pk.segment_pairs = 0;
+    pk.grid.clear();
+    pk.grid_cells = pk.grid_rows = pk.grid_cols = 0;
+    pk.n_cc_local = pk.n_cc_sweep = 0;
+    pk.local_rows = pk.local_cols = 0;
     // Per pair: its shape, work items and sort key.  Accurate-variant pairs go
     // first (they run in their own launch), then within each variant the
     // largest items first, so that the persistent grid's tail is made of small
@@ -403,6 +411,7 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
     pk.tasks.resize((size_t)n);
     pk.item_begin.assign((size_t)n + 1, 0);
     pk.n_acc_items = 0;
+    pk.n_acc_tasks = 0;
     pk.n_chunks = 0;
     for (int64_t k = 0; k < n; ++k) {
         const int64_t p = order[(size_t)k];
@@ -423,7 +432,16 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
             t.tile_rows = q.tile_rows;
             t.col_tiles = q.col_tiles;
             t.accurate = q.accurate;
-            if (ctx->opt.method == LK_METHOD_CC && (int64_t)q.n_rows * q.n_cols >= kCcGridMin) {
+            const bool cc = ctx->opt.method == LK_METHOD_CC;
+            const int search = ctx->opt.cc_search;
+            const bool fits = q.n_rows <= lk::kCcLocalMax && q.n_cols <= lk::kCcLocalMax;
+            if (cc && search != LK_CC_SEARCH_SWEEP && fits) {
+                t.cc_grid = 2;
+                ++pk.n_cc_local;
+                pk.local_rows = std::max(pk.local_rows, q.n_rows);
+                pk.local_cols = std::max(pk.local_cols, q.n_cols);
+            } else if (cc && (search == LK_CC_SEARCH_BINNED ||
+                              (search == LK_CC_SEARCH_AUTO && (int64_t)q.n_rows * q.n_cols >= kCcGridMin))) {
                 // at most about 2 sqrt(N) cells per side; the device takes fewer
                 // where the segments are long (cells about 1.5 segment lengths)
                 const int64_t want = 2 * (int64_t)std::ceil(std::sqrt((double)std::max(q.n_rows, q.n_cols)));
@@ -434,6 +452,8 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
                 pk.grid_cells = std::max<int64_t>(pk.grid_cells, (int64_t)G * G);
                 pk.grid_rows = std::max<int64_t>(pk.grid_rows, q.n_rows);
                 pk.grid_cols = std::max<int64_t>(pk.grid_cols, q.n_cols);
+            } else if (cc) {
+                ++pk.n_cc_sweep;
             }
             const int64_t full = q.n_rows / q.tile_rows, last = q.n_rows - full * q.tile_rows;
             const int64_t chunks_per_col = full * ((q.tile_rows + lk::kChunkRows - 1) / lk::kChunkRows) +
@@ -442,7 +462,10 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
         }
         pk.tasks[(size_t)k] = t;
         pk.item_begin[(size_t)k + 1] = pk.item_begin[(size_t)k] + q.items;
-        if (q.accurate) pk.n_acc_items = pk.item_begin[(size_t)k + 1];
+        if (q.accurate) {
+            pk.n_acc_items = pk.item_begin[(size_t)k + 1];
+            pk.n_acc_tasks = k + 1;
+        }
     }
     pk.n_items = pk.item_begin[(size_t)n];
     if (pk.n_items > (int64_t)INT32_MAX * 16)
@@ -473,7 +496,7 @@ size_t grid_bytes(const Packed* pk) {
 size_t workspace_bytes(const lk_ctx* ctx, int64_t n_tasks, int64_t n_items, int64_t n_chunks, const Packed* pk) {
     const size_t near = (size_t)std::max(0, ctx->opt.near_capacity);
     const size_t cc = ctx->opt.method == LK_METHOD_CC ? (size_t)std::max(1, ctx->opt.cc_capacity) : 0;
-    return n_tasks * (sizeof(PairTask) + 8 + 8 + 8 + 4 + 4 + 8 + 4 + (cc ? 4 : 0)) + n_items * (4 + 8 + 8 + 8) +
+    return n_tasks * (sizeof(PairTask) + 8 + 8 + 8 + 4 + 4 + 8 + 4 + (cc ? 4 + 4 : 0)) + n_items * (4 + 8 + 8 + 8) +
            chunk_capacity(ctx->opt, n_chunks) * sizeof(lk::CarefulChunk) +
            (near + cc) * sizeof(NearEntry) + grid_bytes(pk) + 80;
 }
@@ -505,6 +528,8 @@ lk_status ensure_workspace(lk_ctx* ctx, Workspace& ws, int64_t n_tasks, int64_t 
     if (ctx->opt.method == LK_METHOD_CC) {
         LK_CUDA(ctx, ws.cc_list.ensure((size_t)std::max(1, ctx->opt.cc_capacity)));
         LK_CUDA(ctx, ws.cc_half.ensure(nt));
+        LK_CUDA(ctx, ws.flag_scan.ensure(nt + 1));
+        LK_CUDA(ctx, ws.flag_sums.ensure(nt / 4096 + 2));
         if (pk && !pk->grid.empty()) {
             LK_CUDA(ctx, ws.grid_offsets.ensure((size_t)pk->grid_cells + 1));
             LK_CUDA(ctx, ws.grid_cursor.ensure((size_t)pk->grid_cells));
@@ -566,7 +591,7 @@ lk::SweepArgs sweep_args(const lk_ctx* ctx, Workspace& ws, const Packed& pk) {
         a.cc_count = ws.counters.p + 9;
         a.cc_capacity = (int)std::min<size_t>(ws.cc_list.cap, (size_t)INT32_MAX);
         a.cc_half = ws.cc_half.p;
-        a.skip_unflagged = 1;
+        a.flag_scan = ws.flag_scan.p;
     }
     return a;
 }
@@ -606,7 +631,14 @@ lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStrea
             if (cc) {
                 // counting crossings first; the direct sum then runs only on the
                 // pairs it flagged (its sweeps skip every other item)
-                lk::launch_cc_sweep(a, ws.counters.p + 8, ctx->num_sms * lk::cc_sweep_blocks_per_sm(), s);
+                if (pk.n_cc_sweep > 0)
+                    lk::launch_cc_sweep(a, ws.counters.p + 8, ctx->num_sms * lk::cc_sweep_blocks_per_sm(), s);
+                if (pk.n_cc_local > 0) {
+                    int G = 1;
+                    while (G < lk::kCcLocalGridMax && G * G < pk.local_rows) G <<= 1;
+                    const lk::CcLocalShape S{pk.local_rows, pk.local_cols, G, lk::kCcLocalEntries * pk.local_rows};
+                    lk::launch_cc_local(a, n, S, s);
+                }
                 if (!pk.grid.empty()) {
                     const lk::CcGridWork w{ws.grid_offsets.p, ws.grid_cursor.p, ws.grid_sums.p, ws.grid_entries.p,
                                            (int64_t)std::min<size_t>(ws.grid_entries.cap, (size_t)INT32_MAX),
@@ -617,9 +649,10 @@ lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStrea
                 }
                 lk::launch_cc_resolve(a, ctx->num_sms * 4, s);
             }
-            lk::launch_sweep_mixed(a, true, 0, pk.n_acc_items, ws.counters.p + 0,
+            if (cc) lk::launch_cc_flag_scan(a, ws.flag_scan.p, ws.flag_sums.p, s);
+            lk::launch_sweep_mixed(a, true, 0, pk.n_acc_items, 0, pk.n_acc_tasks, ws.counters.p + 0,
                                    ctx->num_sms * lk::sweep_mixed_blocks_per_sm(true), s);
-            lk::launch_sweep_mixed(a, false, pk.n_acc_items, pk.n_items, ws.counters.p + 4,
+            lk::launch_sweep_mixed(a, false, pk.n_acc_items, pk.n_items, pk.n_acc_tasks, n, ws.counters.p + 4,
                                    ctx->num_sms * lk::sweep_mixed_blocks_per_sm(false), s);
             if (ctx->opt.timing) LK_CUDA(ctx, record_event(ws.ev1, s));
             const bool fast = pk.n_items > pk.n_acc_items, acc = pk.n_acc_items > 0;
@@ -716,6 +749,7 @@ void lk_default_options(lk_options* opt) {
     opt->accurate_threshold = (int64_t)1 << 22;
     opt->method = LK_METHOD_DS;
     opt->cc_capacity = 1 << 18;
+    opt->cc_search = LK_CC_SEARCH_AUTO;
 }
 
 const char* lk_last_error(const lk_ctx* ctx) {
@@ -739,6 +773,7 @@ lk_status lk_create(lk_ctx** out, const void* vertices, lk_dtype vdtype, int64_t
         (o.precision != LK_MIXED && o.precision != LK_ALL_F64) || o.tile_rows < 0 ||
         o.near_capacity < 1 || o.accurate_threshold < 0 || o.chunk_capacity < 1 ||
         (o.method != LK_METHOD_DS && o.method != LK_METHOD_CC) || o.cc_capacity < 1 ||
+        o.cc_search < LK_CC_SEARCH_AUTO || o.cc_search > LK_CC_SEARCH_BINNED ||
         (o.method == LK_METHOD_CC && o.precision != LK_MIXED))
         return fail(nullptr, LK_ERR_ARG,
                     "lk_create: invalid options (near_ratio >= 3, 0 < int_tol < 0.5; LK_METHOD_CC needs LK_MIXED)");

@@ -65,7 +65,8 @@ struct PairTask {
     int32_t out_index;   // position of the pair in the caller's list
     int32_t status;      // LK_OK, or LK_ERR_ARG for an invalid pair (then it has no items)
     int32_t accurate;    // 1: bias-free FP32 arithmetic variant (large pairs)
-    int32_t cc_grid;     // counting crossings: 1 when the pair's candidates come from the binned search
+    int32_t cc_grid;     // counting crossings: 1 when the pair's candidates come from the binned
+                         // search over the device grid, 2 from the one-CTA search, else 0
     float row_off[4];    // frame offset of the row loop's vertices ([3] unused)
     float col_off[4];    // frame offset of the column loop's vertices ([3] unused)
     float scale;         // power of two
@@ -117,7 +118,8 @@ struct SweepArgs {
     unsigned long long* cc_count;  // [1] candidates found (may exceed the list's capacity)
     int cc_capacity;
     int* cc_half;                  // [n_tasks] twice the linking number by crossings
-    int skip_unflagged;            // direct-sum sweeps: only items of pairs flagged kFlagCcFallback
+    const unsigned int* flag_scan; // [n_tasks+1] exclusive scan of the item counts of pairs flagged
+                                   // kFlagCcFallback; set: the direct-sum sweeps visit only those items
 };
 
 // One request's contiguous run of items inside a serving wave.
@@ -153,8 +155,8 @@ cudaError_t launch_loop_boxes(Vtx* V, const int64_t* offsets, int64_t n_loops, i
                               unsigned long long* keys, unsigned long long* next_keys, double* aabb, float4* R,
                               const void* data, int dtype, int is_delta, cudaStream_t s);
 void launch_pair_frames(PairTask* tasks, int64_t n_tasks, const double* aabb, cudaStream_t s);
-void launch_sweep_mixed(const SweepArgs& a, bool accurate, int64_t item_lo, int64_t item_hi,
-                        unsigned long long* counter, int grid, cudaStream_t s);
+void launch_sweep_mixed(const SweepArgs& a, bool accurate, int64_t item_lo, int64_t item_hi, int64_t task_lo,
+                        int64_t task_hi, unsigned long long* counter, int grid, cudaStream_t s);
 void launch_sweep_f64(const SweepArgs& a, int grid, cudaStream_t s);
 // The careful passes of each arithmetic variant; a variant without work items
 // in the call is not launched.
@@ -184,6 +186,21 @@ struct CcGridWork {
     int* G;                    // [1]: the pair's grid size, chosen on the device
     unsigned long long* total; // [1]: the pair's entries, counted in 64 bits
 };
+// Counting crossings of pairs whose loops both have at most kCcLocalMax
+// segments (cc_grid == 2): one CTA per pair, everything in shared memory.
+constexpr int kCcLocalMax = 2048;
+constexpr int kCcLocalGridMax = 64;     // grid cells per side at most
+constexpr int kCcLocalEntries = 4;      // row-segment entries per row segment
+struct CcLocalShape {
+    int max_rows, max_cols;             // the largest loops among the pairs
+    int G_max;                          // power of two <= kCcLocalGridMax
+    int entry_cap;                      // kCcLocalEntries * max_rows
+};
+size_t cc_local_smem_bytes(const CcLocalShape& S);
+// Counting crossings: scan[0..n_tasks] = exclusive scan of the item counts of
+// the pairs flagged kFlagCcFallback (block_sums: n_tasks / 4096 + 2 entries).
+void launch_cc_flag_scan(const SweepArgs& a, unsigned int* scan, unsigned int* block_sums, cudaStream_t s);
+void launch_cc_local(const SweepArgs& a, int64_t n_tasks, const CcLocalShape& S, cudaStream_t s);
 // G_max: the allocated grid size (offsets hold G_max^2 + 1 counts).
 void launch_cc_grid(const SweepArgs& a, int task, int n_rows, int n_cols, int G_max, const CcGridWork& w,
                     cudaStream_t s);

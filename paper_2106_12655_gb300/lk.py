@@ -30,6 +30,9 @@ LK_MIXED = 0
 LK_ALL_F64 = 1
 LK_METHOD_DS = 0
 LK_METHOD_CC = 1
+LK_CC_SEARCH_AUTO = 0
+LK_CC_SEARCH_SWEEP = 1
+LK_CC_SEARCH_BINNED = 2
 
 STATUS_NAMES = {0: "LK_OK", 1: "LK_ERR_ARG", 2: "LK_ERR_ZERO_SEGMENT", 3: "LK_ERR_INTERSECT",
                 4: "LK_ERR_NONINTEGER", 5: "LK_ERR_OOM", 6: "LK_ERR_TIMEOUT", 7: "LK_ERR_CUDA",
@@ -48,7 +51,7 @@ class lk_options(ctypes.Structure):
                 ("tile_rows", ctypes.c_int), ("near_capacity", ctypes.c_int),
                 ("timing", ctypes.c_int), ("chunk_capacity", ctypes.c_int),
                 ("accurate_threshold", ctypes.c_int64), ("method", ctypes.c_int),
-                ("cc_capacity", ctypes.c_int)]
+                ("cc_capacity", ctypes.c_int), ("cc_search", ctypes.c_int)]
 
 
 class lk_stats(ctypes.Structure):

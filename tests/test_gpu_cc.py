@@ -2,7 +2,9 @@
 linking numbers must equal the FP64 direct-sum oracle's exactly, and a pair
 decided by its crossings returns the exact integer as its raw value.  Pairs
 the projection cannot decide (forced here by a tiny candidate list) fall
-back to the direct sum in the same call."""
+back to the direct sum in the same call.  Each candidate search (the
+all-pairs sweep, the one-CTA binned search, the device-wide grid) must give
+the same results."""
 import numpy as np
 import pytest
 
@@ -51,15 +53,19 @@ def check(g, pairs=None, **opts):
     return lk_o, raw, st
 
 
+SEARCH = {"auto": lk.LK_CC_SEARCH_AUTO, "sweep": lk.LK_CC_SEARCH_SWEEP, "binned": lk.LK_CC_SEARCH_BINNED}
+
+
+@pytest.mark.parametrize("search", list(SEARCH))
 @pytest.mark.parametrize("name", ["ring_chain", "chainmail", "torus_small", "whitehead", "ribbon", "hopf"])
-def test_cc_matches_oracle_and_is_exact(name):
+def test_cc_matches_oracle_and_is_exact(name, search):
     g = {"ring_chain": lambda: W.ring_chain(),
          "chainmail": lambda: W.chainmail(),
          "torus_small": lambda: W.torus_link(5, 7, 3000, dtype=np.float32, n2=2711),
          "whitehead": lambda: W.whitehead(),
          "ribbon": lambda: W.double_helix_ribbon(25, 6000),
          "hopf": lambda: W.hopf(24, 30)}[name]()
-    lk_o, raw, st = check(g)
+    lk_o, raw, st = check(g, cc_search=SEARCH[search])
     # decided by crossings: the raw value is the integer itself
     assert st["cc_fallback_pairs"] == 0
     assert np.array_equal(raw, lk_o.astype(np.float64))
@@ -81,7 +87,8 @@ def test_cc_large_torus_closed_form():
     assert st["cc_fallback_pairs"] == 0 and raw[0] == -31 * 37
 
 
-def test_cc_random_polygons_against_exact_crossings():
+@pytest.mark.parametrize("search", list(SEARCH))
+def test_cc_random_polygons_against_exact_crossings(search):
     import crossings as C
 
     rng = np.random.default_rng(12)
@@ -98,17 +105,18 @@ def test_cc_random_polygons_against_exact_crossings():
         pairs.append([base, base + 1])
         expect.append(lam)
     g = W.from_loops(loops, dtype=np.float64, pairs=pairs)
-    lk_o, raw, status, st = run_cc(g)
+    lk_o, raw, status, st = run_cc(g, cc_search=SEARCH[search])
     assert np.all(status == lk.LK_OK)
     assert np.array_equal(lk_o, np.asarray(expect, np.int32))
 
 
-def test_cc_fallback_to_direct_sum():
+@pytest.mark.parametrize("search", ["sweep", "binned"])
+def test_cc_fallback_to_direct_sum(search):
     """A one-entry candidate list: every pair with more than one candidate is
     computed by the direct sum instead; the linking numbers do not change."""
     g = W.chainmail(rows=6, cols=10, dtype=np.float64)
-    lk_full, raw_full, _ = check(g)
-    lk_o, raw, st = check(g, cc_capacity=1)
+    lk_full, raw_full, _ = check(g, cc_search=SEARCH[search])
+    lk_o, raw, st = check(g, cc_capacity=1, cc_search=SEARCH[search])
     assert np.array_equal(lk_o, lk_full)
     fell_back = raw != lk_o.astype(np.float64)
     assert fell_back.any() and not fell_back.all()
@@ -117,13 +125,14 @@ def test_cc_fallback_to_direct_sum():
     assert np.abs(raw[fell_back] - ref[fell_back]).max() <= 1e-6
 
 
-def test_cc_reports_intersections():
+@pytest.mark.parametrize("search", list(SEARCH))
+def test_cc_reports_intersections(search):
     t = np.arange(64) * 2 * np.pi / 64
     a = np.stack([np.cos(t), np.sin(t), 0 * t], 1)
     b = np.stack([np.cos(t), 0 * t, np.sin(t)], 1)          # shares vertices (+-1,0,0) with a
     c = np.stack([5 + np.cos(t), np.sin(t), 0 * t], 1)
     g = W.from_loops([a, b, c], pairs=[[0, 1], [0, 2]])
-    lk_o, raw, status, st = run_cc(g)
+    lk_o, raw, status, st = run_cc(g, cc_search=SEARCH[search])
     assert status[0] == lk.LK_ERR_INTERSECT and lk_o[0] == 0
     assert status[1] == lk.LK_OK and lk_o[1] == 0 and raw[1] == 0.0
 
@@ -140,5 +149,36 @@ def test_cc_binned_search_matches_oracle(name):
          "whitehead": lambda: W.whitehead(20_000, 30_000)}[name]()
     assert g.segment_pairs() >= 1 << 28
     lk_o, raw, st = check(g)
+    assert st["cc_fallback_pairs"] == 0
+    assert np.array_equal(raw, lk_o.astype(np.float64))
+
+
+@pytest.mark.parametrize("search", ["sweep", "binned"])
+def test_cc_search_boundary_sizes(search):
+    """Loops at and just past the one-CTA limit (2,048 segments), loops of a few
+    segments, a pair whose projections cross but do not link and one whose
+boxes lie apart:
+    every search gives the oracle's linking numbers, decided by crossings."""
+    rng = np.random.default_rng(31)
+    loops, pairs = [], []
+    for n1, n2 in [(2048, 2048), (2049, 2048), (2048, 3000), (3, 5), (4, 2048), (700, 9)]:
+        t1 = np.arange(n1) * 2 * np.pi / n1
+        t2 = np.arange(n2) * 2 * np.pi / n2
+        a = np.stack([np.cos(t1), np.sin(t1), 0.05 * np.sin(3 * t1)], 1)
+        b = np.stack([1 + np.cos(t2), 0.1 * np.sin(2 * t2), np.sin(t2)], 1)
+        a += rng.normal(scale=1e-3, size=a.shape)
+        b += rng.normal(scale=1e-3, size=b.shape)
+        base = len(loops)
+        loops += [a, b]
+        pairs.append([base, base + 1])
+    # a ring above the first one whose projection crosses it (lk = 0 from
+    # crossings that cancel), and one whose box lies apart from it
+    t = np.arange(300) * 2 * np.pi / 300
+    loops.append(np.stack([1.3 + 0.5 * np.cos(t), 0.5 * np.sin(t), 0.3 + 0 * t], 1))
+    pairs.append([0, len(loops) - 1])
+    loops.append(np.stack([2.5 + 0.5 * np.cos(t), 0.5 * np.sin(t), 0 * t], 1))
+    pairs.append([0, len(loops) - 1])
+    g = W.from_loops(loops, dtype=np.float64, pairs=pairs)
+    lk_o, raw, st = check(g, cc_search=SEARCH[search])
     assert st["cc_fallback_pairs"] == 0
     assert np.array_equal(raw, lk_o.astype(np.float64))
