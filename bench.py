@@ -246,9 +246,10 @@ def stress_block(stream):
     4x10^6 segments, 6,250,000 pairs, all lk = 1, from the device's potential
     link search), each verified by the direct sum and by counting crossings.
     Times are CUDA-event medians of the timed verifies after three untimed
-    ones (the first sizes the work lists -- the largest shape gets them sized
-    up front --, the third builds the graph plan of the repeated list, so the
-    timed verifies run that plan); the largest shape is timed once."""
+    ones (the first packs the list and sizes the work lists -- the largest
+    shape gets them sized up front --, the second, the list's first repeat,
+    builds its graph plan, so the timed verifies replay that plan); the
+    largest shape is timed once."""
     import torch
     from paper_2106_12655_gb300 import lk
     from paper_2106_12655_gb300 import workloads as W
@@ -258,7 +259,7 @@ def stress_block(stream):
     for name, make, expect, opts, warm, reps in (
             ("woundball_nu1000", lambda: W.woundball(1000, 500_000), 0, {}, 3, 3),
             ("square_links_1250", lambda: W.square_links(625, 400), 1, {}, 3, 3),
-            ("square_links_5000", lambda: W.square_links(2500, 800), 1, big, 1, 1)):
+            ("square_links_5000", lambda: W.square_links(2500, 800), 1, big, 3, 1)):
         g = make()
         g.vertices = g.vertices.astype(np.float32)
         v = torch.from_numpy(g.vertices).cuda()

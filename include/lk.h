@@ -66,7 +66,8 @@ typedef enum {
     /* direct summation of Eq. 4 over every segment pair (the default) */
     LK_METHOD_DS = 0,
     /* counting crossings of a projection (Sec. 3.4, Method 1; Algorithm 4): an
-     * FP32 sweep over every segment pair finds candidate crossings, FP64
+     * FP32 candidate search (binned, or a sweep over every segment pair: see
+     * lk_cc_search) finds candidate crossings, FP64
      * decides them, and the count of signed crossings gives the linking
      * number exactly; a pair whose projection is not regular within FP64
      * rounding (or whose candidates overflow cc_capacity) is computed by the
@@ -131,7 +132,7 @@ typedef struct lk_stats {
     int64_t careful_items;    /* whole items swept again with per-pair tests (chunk list full) */
     double sweep_ms;          /* bulk sweep kernel time (options.timing = 1), else -1 */
     int64_t careful_chunks;   /* 32-row chunks swept again with per-pair tests */
-    int64_t cc_candidates;    /* LK_METHOD_CC: candidate crossings found by the FP32 sweep */
+    int64_t cc_candidates;    /* LK_METHOD_CC: candidate crossings found by the FP32 search */
     int64_t cc_fallback_pairs;/* LK_METHOD_CC: pairs the crossings could not decide (direct sum) */
 } lk_stats;
 
