@@ -239,6 +239,45 @@ def counting_crossings_block(g, v, off, pairs_d, lk_ref, stream, flush, steps=20
             "exact_integer_raw": bool(np.all(raw_h == lo_h)), "all_status_ok": bool(np.all(st_h == 0))}
 
 
+def per_pair_block(g, v, off, lk_ref, stream, n_sample=512, seed=9):
+    """The sheet verified one pair per call, the structure of the paper's GPU
+    path (one kernel launch per loop pair, Sec. 3.4), against the batched step:
+    a seeded sample of pairs, each through its own lk_verify on device-resident
+    buffers (the call packs the pair and launches its own kernels), timed with
+    CUDA events around the whole sample after one untimed pass; the per-step
+    figure scales the per-pair time to all pairs of the sheet."""
+    import torch
+    from paper_2106_12655_gb300 import lk
+
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(g.pairs.shape[0], min(n_sample, g.pairs.shape[0]), replace=False))
+    sample = [torch.from_numpy(np.ascontiguousarray(g.pairs[k:k + 1])).to(v.device) for k in pick]
+    lo = torch.zeros(len(pick), dtype=torch.int32, device=v.device)
+    raw = torch.zeros(len(pick), dtype=torch.float64, device=v.device)
+    st = torch.zeros(len(pick), dtype=torch.int32, device=v.device)
+    ctx = lk.lk_create(v, off, None, stream)
+    try:
+        for rep_ in range(2):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k, pd in enumerate(sample):
+                lk.lk_verify(ctx, pd, lo[k:k + 1], raw[k:k + 1], st[k:k + 1], stream)
+            e1.record(stream)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        lo_h = lo.cpu().numpy()
+    finally:
+        lk.lk_destroy(ctx)
+    per_pair = ms / len(pick)
+    sps = g.sizes()[g.pairs[pick]].prod(axis=1).sum()
+    return {"pairs_sampled": int(len(pick)), "ms_per_pair": per_pair,
+            "ms_per_step_scaled": per_pair * g.pairs.shape[0],
+            "value": float(sps) / (ms / 1e3), "unit": UNIT,
+            "lk_equal_batched": bool(np.array_equal(lo_h, lk_ref[pick])),
+            "all_status_ok": bool(np.all(st.cpu().numpy() == 0))}
+
+
 def stress_block(stream):
     """The paper's large-input stress shapes (Sec. 4, Table 1): a woundball
     (nu = 10^3, 10^6 segments in two loops, lk = 0) and the two thick square
@@ -563,6 +602,7 @@ def run_ours(args):
         "clocks": clk, "wall_s_timed_region": wall,
     }
     if world == 1:
+        line["one_call_per_pair"] = per_pair_block(g, v, off, lk_host, stream)
         line["counting_crossings"] = counting_crossings_block(g, v, off, pairs_d, lk_host, stream, flush)
         line["counting_crossings_all_pairs_sweep"] = counting_crossings_block(
             g, v, off, pairs_d, lk_host, stream, flush, search=lk.LK_CC_SEARCH_SWEEP)
