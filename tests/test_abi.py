@@ -51,6 +51,7 @@ def test_default_options(lib):
     assert o.int_tol == 0.1
     assert o.near_capacity == 1 << 20
     assert o.method == lk.LK_METHOD_DS and o.cc_capacity == 1 << 18
+    assert o.cc_search == lk.LK_CC_SEARCH_AUTO
 
 
 def _create_status(v, off, opt=None):
@@ -77,6 +78,11 @@ def test_create_rejects_bad_geometry_before_device_work(lib):
     o = lk.lk_default_options()
     o.method = 7
     assert _create_status(v, np.array([0, 5, 10], np.int64), o) == lk.LK_ERR_ARG
+    for bad_search in (-1, 3):
+        o = lk.lk_default_options()
+        o.method = lk.LK_METHOD_CC
+        o.cc_search = bad_search
+        assert _create_status(v, np.array([0, 5, 10], np.int64), o) == lk.LK_ERR_ARG
 
 
 def test_create_rejects_zero_length_segments(lib):
