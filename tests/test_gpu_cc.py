@@ -182,3 +182,33 @@ boxes lie apart:
     lk_o, raw, st = check(g, cc_search=SEARCH[search])
     assert st["cc_fallback_pairs"] == 0
     assert np.array_equal(raw, lk_o.astype(np.float64))
+
+
+def test_cc_one_cta_search_many_candidates():
+    """An interwound pair of loops under the one-CTA limit (2,000 and 1,999
+    segments, nu = 20: about 600 projected crossings) produces more candidates
+    than a CTA buffers (256); the rest go to the list directly.  lk = 0 from
+    crossings that cancel, raw exact."""
+    g = W.woundball(20, 2000, n2=1999)
+    lk_o, raw, st = check(g)
+    assert st["cc_candidates"] > 256 and st["cc_fallback_pairs"] == 0
+    assert lk_o[0] == 0 and raw[0] == 0.0
+
+
+def test_cc_one_cta_search_halves_its_grid():
+    """A row loop that zigzags across the whole intersection of the two loops'
+    boxes: at the starting grid (16 x 16) its segments' entries exceed four per
+    segment, so the grid halves (down to 2 x 2) before the binning; the result
+    still equals the oracle's, decided by crossings."""
+    n_zz = 128
+    ys = np.linspace(-1, 1, n_zz)
+    xs = np.where(np.arange(n_zz) % 2 == 0, -1.0, 1.0)
+    zz = np.stack([xs, ys, 0.05 * np.sin(np.arange(n_zz))], 1)
+    ret = np.stack([np.full(8, 1.6), np.linspace(1, -1, 8), np.zeros(8)], 1)   # return path
+    a = np.concatenate([zz, ret], 0)
+    t = np.arange(300) * 2 * np.pi / 300
+    b = np.stack([0.2 + 0.9 * np.cos(t), 0.1 * np.sin(3 * t), 0.9 * np.sin(t)], 1)
+    g = W.from_loops([a, b], pairs=[[0, 1]])
+    for search in ("auto", "sweep"):
+        lk_o, raw, st = check(g, cc_search=SEARCH[search])
+        assert st["cc_fallback_pairs"] == 0 and raw[0] == lk_o[0] == -1
