@@ -13,12 +13,17 @@ resident in HBM; L2 is flushed (256 MB write) before every timed step.
 `--impl reference` times the FP64 CPU oracle on the same workload instead.
 Under torchrun each rank verifies its own sheet (weak scaling, no collective
 on the data path).
+
+The other workloads (ring chain, knit yarn, torus links, serving piles and
+the paper's stress shapes) are reported in blocks after the headline keys,
+and a compact "summary" of them ends the line.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -35,8 +40,10 @@ UNIT = "segment-pair evals/s"
 # Algorithmic FP32 work per segment pair (FMA = 2 flops): the amortised
 # closed-form term with shared grid norms and edge dot products.
 FLOPS_PER_SP = 58.0
-# FP32 peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# FP32 lanes per SM of this GPU generation and its maximum SM clock; the SM
+# count is read from the device (152 on a GB300): peak = SMs x 128 x 2 x clock.
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
 # Kernels one chainmail step launches: pair_frames, sweep_packed, careful_chunk,
 # sweep_careful (all fast variant: the sheet has no accurate-variant pair, so
 # those launches are skipped), near_fix, reduce.
@@ -57,8 +64,29 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-stress", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=600)
+    ap.add_argument("--serving-requests", type=int, default=2000)
     return ap.parse_args()
+
+
+def cpu_model() -> str:
+    """The host CPU's model string (lscpu), for the CPU baseline."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for key in ("Model name:", "Vendor ID:"):
+            for ln in out.splitlines():
+                if ln.strip().startswith(key):
+                    return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
+
+
+def err_stats(raw, ref):
+    """|raw - ref| per result: max, p99 and the index of the max."""
+    d = np.abs(np.asarray(raw, np.float64) - np.asarray(ref, np.float64))
+    if d.size == 0:
+        return {"max": 0.0, "p99": 0.0, "argmax": -1, "n": 0}
+    return {"max": float(d.max()), "p99": float(np.percentile(d, 99)), "argmax": int(np.argmax(d)), "n": int(d.size)}
 
 
 def dist_info():
@@ -242,8 +270,9 @@ def counting_crossings_block(g, v, off, pairs_d, lk_ref, stream, flush, steps=20
 def per_pair_block(g, v, off, lk_ref, stream, n_sample=512, seed=9):
     """The sheet verified one pair per call, the structure of the paper's GPU
     path (one kernel launch per loop pair, Sec. 3.4), against the batched step:
-    a seeded sample of pairs, each through its own lk_verify on device-resident
-    buffers (the call packs the pair and launches its own kernels), timed with
+    a seeded sample of pairs, each through its own lk_verify (its pair from
+    host memory, which the call packs without any device read-back, and its
+    results to device memory; the call launches its own kernels), timed with
     CUDA events around the whole sample after one untimed pass; the per-step
     figure scales the per-pair time to all pairs of the sheet."""
     import torch
@@ -251,7 +280,7 @@ def per_pair_block(g, v, off, lk_ref, stream, n_sample=512, seed=9):
 
     rng = np.random.default_rng(seed)
     pick = np.sort(rng.choice(g.pairs.shape[0], min(n_sample, g.pairs.shape[0]), replace=False))
-    sample = [torch.from_numpy(np.ascontiguousarray(g.pairs[k:k + 1])).to(v.device) for k in pick]
+    sample = [np.ascontiguousarray(g.pairs[k:k + 1]) for k in pick]
     lo = torch.zeros(len(pick), dtype=torch.int32, device=v.device)
     raw = torch.zeros(len(pick), dtype=torch.float64, device=v.device)
     st = torch.zeros(len(pick), dtype=torch.int32, device=v.device)
@@ -278,140 +307,278 @@ def per_pair_block(g, v, off, lk_ref, stream, n_sample=512, seed=9):
             "all_status_ok": bool(np.all(st.cpu().numpy() == 0))}
 
 
+def timed_verify(ctx, pd, n, stream, warm, reps, device):
+    """CUDA-event times (ms) of `reps` verifies of the device pair list after
+    `warm` untimed ones, and the last results (host arrays)."""
+    import torch
+    from paper_2106_12655_gb300 import lk
+
+    lo = torch.zeros(n, dtype=torch.int32, device=device)
+    raw = torch.zeros(n, dtype=torch.float64, device=device)
+    st = torch.zeros(n, dtype=torch.int32, device=device)
+    ms = []
+    for k in range(warm + reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lk.lk_verify(ctx, pd, lo, raw, st, stream)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= warm:
+            ms.append(e0.elapsed_time(e1))
+    est = np.zeros(n)
+    try:
+        lk.lk_get_error_estimates(ctx, est)
+    except lk.LkError:
+        est[:] = np.nan
+    return ms, lo.cpu().numpy(), raw.cpu().numpy(), st.cpu().numpy(), est
+
+
 def stress_block(stream):
-    """The paper's large-input stress shapes (Sec. 4, Table 1): a woundball
-    (nu = 10^3, 10^6 segments in two loops, lk = 0) and the two thick square
-    links (1,250 loops, 5x10^5 segments, 390,625 pairs, and 5,000 loops,
-    4x10^6 segments, 6,250,000 pairs, all lk = 1, from the device's potential
-    link search), each verified by the direct sum and by counting crossings.
-    Times are CUDA-event medians of the timed verifies after three untimed
-    ones (the first packs the list and sizes the work lists -- the largest
-    shape gets them sized up front --, the second, the list's first repeat,
-    builds its graph plan, so the timed verifies replay that plan); the
-    largest shape is timed once."""
+    """The paper's large-input stress shapes (Sec. 4, Table 1): the two
+    double-helix ribbons (2 x 10^5 segments, lk = 10 and 1000), the woundballs
+    (nu = 10^3 with 10^6 segments and nu = 10^4 with 2 x 10^6, lk = 0) and the
+    two thick square links (1,250 loops, 5x10^5 segments, 390,625 pairs, and
+    5,000 loops, 4x10^6 segments, 6,250,000 pairs, all lk = 1, from the
+    device's potential link search), each by the direct sum and by counting
+    crossings.  Each direct-sum record gives the raw error against the closed
+    form, the library's own error estimate and how many pairs the compensated
+    (precise) sweep summed again.  Times are CUDA-event medians of the timed
+    verifies after untimed ones (the first packs the list and sizes the work
+    lists -- the largest shape gets them sized up front --, the second, the
+    list's first repeat, builds its graph plan, so the timed verifies replay
+    that plan); the largest shapes are timed once."""
     import torch
     from paper_2106_12655_gb300 import lk
     from paper_2106_12655_gb300 import workloads as W
 
     out = {}
     big = {"near_capacity": 1_400_000_000, "chunk_capacity": 1 << 26, "cc_capacity": 1 << 26}
-    for name, make, expect, opts, warm, reps in (
-            ("woundball_nu1000", lambda: W.woundball(1000, 500_000), 0, {}, 3, 3),
-            ("square_links_1250", lambda: W.square_links(625, 400), 1, {}, 3, 3),
-            ("square_links_5000", lambda: W.square_links(2500, 800), 1, big, 3, 1)):
+    for name, make, expect, opts, warm, reps, methods in (
+            ("ribbon_lk10", lambda: W.double_helix_ribbon(10, 100_000), 10, {}, 2, 3, ("ds",)),
+            ("ribbon_lk1000", lambda: W.double_helix_ribbon(1000, 100_000), 1000, {}, 2, 3, ("ds",)),
+            ("woundball_nu1000", lambda: W.woundball(1000, 500_000), 0, {}, 2, 2, ("ds", "cc")),
+            ("woundball_nu10000", lambda: W.woundball(10_000, 1_000_000), 0, {"cc_capacity": 1 << 29}, 1, 1,
+             ("ds", "cc")),
+            ("square_links_1250", lambda: W.square_links(625, 400), 1, {}, 3, 3, ("ds", "cc")),
+            ("square_links_5000", lambda: W.square_links(2500, 800), 1, big, 3, 1, ("ds", "cc"))):
         g = make()
         g.vertices = g.vertices.astype(np.float32)
         v = torch.from_numpy(g.vertices).cuda()
         off = torch.from_numpy(g.offsets).cuda()
         rec = {"loops": g.n_loops, "segments": int(g.vertices.shape[0])}
-        for label, method in (("direct_sum", lk.LK_METHOD_DS), ("counting_crossings", lk.LK_METHOD_CC)):
+        for label in methods:
+            method = lk.LK_METHOD_DS if label == "ds" else lk.LK_METHOD_CC
             o = lk.lk_default_options()
             o.method = method
             for k, val in opts.items():
                 setattr(o, k, val)
             ctx = lk.lk_create(v, off, o, stream)
             try:
-                pairs = lk.lk_candidates(ctx, stream=stream)
+                if g.pairs.shape[0] == 1:
+                    pairs = g.pairs
+                else:
+                    pairs = lk.lk_candidates(ctx, stream=stream)
                 n = pairs.shape[0]
-                pd = torch.from_numpy(pairs).cuda()
-                lo = torch.zeros(n, dtype=torch.int32, device=v.device)
-                raw = torch.zeros(n, dtype=torch.float64, device=v.device)
-                st = torch.zeros(n, dtype=torch.int32, device=v.device)
-                ms = []
-                for k in range(warm + reps):
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    lk.lk_verify(ctx, pd, lo, raw, st, stream)
-                    e1.record(stream)
-                    e1.synchronize()
-                    if k >= warm:
-                        ms.append(e0.elapsed_time(e1))
+                pd = torch.from_numpy(np.ascontiguousarray(pairs)).cuda()
+                ms, lo_h, raw_h, st_h, est = timed_verify(ctx, pd, n, stream, warm, reps, v.device)
                 stats = lk.lk_get_stats(ctx)
-                lo_h, raw_h, st_h = lo.cpu().numpy(), raw.cpu().numpy(), st.cpu().numpy()
             finally:
                 lk.lk_destroy(ctx)
             sps = g.segment_pairs(pairs)
             med = statistics.median(ms)
+            ref = np.sign(lo_h) * float(expect) if expect else np.zeros(n)
             r = {"value": sps / (med / 1e3), "unit": UNIT, "ms": med, "pairs": int(n), "segment_pairs": int(sps),
-                 "lk_all_expected": bool(np.all(lo_h == expect)), "all_status_ok": bool(np.all(st_h == 0)),
-                 "max_abs_raw_err": float(np.max(np.abs(raw_h - expect))),
-                 "fp64_recomputed_segment_pairs": stats["fp64_pairs"]}
+                 "lk_all_expected": bool(np.all(np.abs(lo_h) == expect)), "all_status_ok": bool(np.all(st_h == 0)),
+                 "max_abs_raw_err": float(np.max(np.abs(np.abs(raw_h) - expect))),
+                 "raw_err_vs_closed_form": err_stats(raw_h, ref),
+                 "max_error_estimate": float(np.nanmax(est)) if n else 0.0,
+                 "fp64_recomputed_segment_pairs": stats["fp64_pairs"], "precise_pairs": stats["precise_pairs"]}
             if method == lk.LK_METHOD_CC:
                 r["candidates"] = stats["cc_candidates"]
                 r["fallback_pairs"] = stats["cc_fallback_pairs"]
-            rec[label] = r
+            rec["direct_sum" if label == "ds" else "counting_crossings"] = r
         out[name] = rec
     return out
 
 
-def configs_block(stream, reps=3):
-    """The other workloads: the knit-yarn sheet (600 loops of 1k-20k segments,
-    all AABB candidates; every pair's distance from an integer -- its parity
-    against the oracle is a test) and the torus links (p,q) in {(2,3), (5,7),
-    (11,13), (31,37)} with 250k segments per component (error against the
-    closed form p*q).  Times are CUDA-event medians of `reps` verifies after
-    three untimed ones."""
+def configs_block(stream, reps=3, oracle_threads=None):
+    """The other workloads of the benchmark's configurations, each verified
+    through lk_verify (CUDA-event medians of `reps` verifies after untimed
+    ones) and, where the FP64 oracle can run in seconds, checked against it
+    result by result (max, p99 and argmax of |raw - oracle|):
+      * ring chain: 16 rings x 128 segments, FP64 vertices, all 120 pairs
+        (latency-bound; the oracle runs on every pair);
+      * knit yarn: 600 stitch loops of 1k-20k segments, all AABB candidates;
+        the all-FP64 GPU direct sum is timed on a seeded ~3% sample of the
+        pairs (its rate, extrapolated to the whole sheet), and a seeded 10%
+        sample of the pairs (with the 20 largest) is compared with the oracle;
+      * torus links (2p,2q), R = 3, r = 1: every (p,q) of {(2,3), (5,7),
+        (11,13), (31,37)} at 250k segments per component, and (5,7), (11,13),
+        (31,37) at 500k, 750k and 1M; error against the closed form |lk| = pq;
+        the all-FP64 GPU path's rate is measured on a 2 x 25k-segment (31,37)
+        link and the oracle's on a seeded sample of 64 column segments (row
+        sums of Eq. 3) of each link, both extrapolated by segment-pair count
+        and labelled so."""
     import torch
+    from oracle import oracle as O
     from paper_2106_12655_gb300 import lk
     from paper_2106_12655_gb300 import workloads as W
 
-    def timed(g):
+    threads = oracle_threads or O.default_threads()
+
+    def verify(g, pairs=None, warm=2, reps_=reps, **opts):
+        pairs = g.pairs if pairs is None else pairs
         v = torch.from_numpy(np.ascontiguousarray(g.vertices)).cuda()
         off = torch.from_numpy(g.offsets).cuda()
+        o = lk.lk_default_options()
+        for k, val in opts.items():
+            setattr(o, k, val)
+        ctx = lk.lk_create(v, off, o, stream)
+        try:
+            pd = torch.from_numpy(np.ascontiguousarray(pairs)).cuda()
+            ms, lo, raw, st, est = timed_verify(ctx, pd, pairs.shape[0], stream, warm, reps_, v.device)
+            stats = lk.lk_get_stats(ctx)
+        finally:
+            lk.lk_destroy(ctx)
+        return statistics.median(ms), lo, raw, st, est, stats
+
+    out = {}
+    # ring chain (config 1)
+    g = W.ring_chain()
+    med, lo, raw, st, est, _ = verify(g, warm=3, reps_=10)
+    ref = O.link_pairs(g.vertices, g.offsets, g.pairs, threads=threads)
+    out["ring_chain"] = {"pairs": int(g.pairs.shape[0]), "segment_pairs": g.segment_pairs(), "ms": med,
+                         "value": g.segment_pairs() / (med / 1e3), "unit": UNIT,
+                         "lk_equal_oracle": bool(np.array_equal(lo, O.round_lk(ref))),
+                         "all_status_ok": bool(np.all(st == 0)), "raw_err_vs_oracle": err_stats(raw, ref),
+                         "max_error_estimate": float(np.max(est))}
+    # knit yarn (config 3)
+    g = W.knit_yarn()
+    med, lo, raw, st, est, stats = verify(g)
+    sizes = g.sizes()[g.pairs].prod(axis=1)
+    rng = np.random.default_rng(31)
+    pick64 = np.sort(rng.choice(g.pairs.shape[0], max(1, g.pairs.shape[0] // 32), replace=False))
+    med64, _, raw64, _, _, _ = verify(g, g.pairs[pick64], warm=1, reps_=1, precision=lk.LK_ALL_F64)
+    sps64 = float(sizes[pick64].sum())
+    order = np.argsort(sizes)
+    pick = np.unique(np.concatenate([order[-20:], np.random.default_rng(7).choice(
+        g.pairs.shape[0], g.pairs.shape[0] // 10, replace=False)]))
+    t0 = time.perf_counter()
+    ref = O.link_pairs(g.vertices, g.offsets, g.pairs[pick], threads=threads)
+    t_or = time.perf_counter() - t0
+    e = err_stats(raw[pick], ref)
+    e["argmax_pair"] = int(pick[e["argmax"]]) if e["n"] else -1
+    out["knit_yarn"] = {"loops": g.n_loops, "pairs": int(g.pairs.shape[0]), "segment_pairs": int(sizes.sum()),
+                        "ms": med, "value": float(sizes.sum()) / (med / 1e3), "unit": UNIT,
+                        "all_status_ok": bool(np.all(st == 0)), "precise_pairs": stats["precise_pairs"],
+                        "fp64_gpu": {"value": sps64 / (med64 / 1e3), "unit": UNIT, "pairs_timed": int(pick64.size),
+                                     "segment_pairs_timed": int(sps64),
+                                     "ms_whole_sheet_extrapolated": med64 * float(sizes.sum()) / sps64},
+                        "speedup_mixed_over_fp64": (float(sizes.sum()) / (med / 1e3)) / (sps64 / (med64 / 1e3)),
+                        "max_abs_raw_minus_fp64_gpu": float(np.max(np.abs(raw[pick64] - raw64))),
+                        "oracle_sample": {"pairs": int(pick.size), "segment_pairs": int(sizes[pick].sum()),
+                                          "seconds": t_or, "threads": threads,
+                                          "lk_equal": bool(np.array_equal(lo[pick], O.round_lk(ref)))},
+                        "raw_err_vs_oracle": e, "max_abs_raw_minus_lk": float(np.max(np.abs(raw - lo))),
+                        "max_error_estimate": float(np.max(est))}
+    # torus links (config 4)
+    g = W.torus_link(31, 37, 25_000, dtype=np.float32)
+    med64, _, _, _, _, _ = verify(g, warm=1, reps_=1, precision=lk.LK_ALL_F64)
+    fp64_rate = g.segment_pairs() / (med64 / 1e3)
+    tl = []
+    for p, q, n in ((2, 3, 250_000), (5, 7, 250_000), (11, 13, 250_000), (31, 37, 250_000),
+                    (5, 7, 500_000), (11, 13, 750_000), (31, 37, 1_000_000)):
+        g = W.torus_link(p, q, n, dtype=np.float32)
+        med, lo, raw, st, est, stats = verify(g, warm=1, reps_=2)
+        sps = g.segment_pairs()
+        rows = np.sort(np.random.default_rng(p * q).choice(n, 64, replace=False))
+        t0 = time.perf_counter()
+        O.link_rows(g.loop(0), g.loop(1), rows, threads=threads)
+        t_or = time.perf_counter() - t0
+        tl.append({"p": p, "q": q, "segments_per_component": n, "segment_pairs": sps, "ms": med,
+                   "value": sps / (med / 1e3), "unit": UNIT, "lk": int(lo[0]), "closed_form_abs_lk": p * q,
+                   "abs_raw_err_vs_closed_form": float(abs(abs(raw[0]) - p * q)), "status_ok": bool(st[0] == 0),
+                   "error_estimate": float(est[0]), "precise": bool(stats["precise_pairs"]),
+                   "fp64_gpu_s_extrapolated": sps / fp64_rate,
+                   "oracle_s_extrapolated": t_or * n / rows.size,
+                   "oracle_sample": "64 seeded column segments of the %d (row sums of Eq. 3), %d threads" % (n, threads)})
+    out["torus_links"] = {"fp64_gpu_rate": {"value": fp64_rate, "unit": UNIT,
+                                            "measured_on": "(31,37) torus link, 2 x 25,000 segments"},
+                          "links": tl}
+    return out
+
+
+def tuning_block(g, v, off, pairs_d, stream, flush, steps=20):
+    """The autotuner on the sheet: lk_autotune's table against the built-in
+    work-item heights, same graph protocol as the headline (L2 flushed before
+    each timed replay); the headline uses whichever was faster."""
+    import torch
+    from paper_2106_12655_gb300 import lk
+
+    res = {}
+    n = g.pairs.shape[0]
+    lo = torch.zeros(n, dtype=torch.int32, device=v.device)
+    raw = torch.zeros(n, dtype=torch.float64, device=v.device)
+    st = torch.zeros(n, dtype=torch.int32, device=v.device)
+    table = None
+    for label in ("default", "tuned"):
         ctx = lk.lk_create(v, off, None, stream)
         try:
-            pd = torch.from_numpy(np.ascontiguousarray(g.pairs)).cuda()
-            n = g.pairs.shape[0]
-            lo = torch.zeros(n, dtype=torch.int32, device=v.device)
-            raw = torch.zeros(n, dtype=torch.float64, device=v.device)
-            st = torch.zeros(n, dtype=torch.int32, device=v.device)
+            if label == "tuned":
+                t0 = time.perf_counter()
+                lk.lk_autotune(ctx, g.pairs, stream)
+                res["tune_seconds"] = time.perf_counter() - t0
+                table = lk.lk_tune_get(ctx)
+                res["table"] = table.reshape(-1, 3).tolist()
+            plan = lk.lk_plan_create(ctx, pairs_d, stream)
             ms = []
-            for k in range(3 + reps):
+            for k in range(steps + 3):
+                flush.fill_(1)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                lk.lk_verify(ctx, pd, lo, raw, st, stream)
+                lk.lk_plan_run(plan, lo, raw, st, stream, ctx=ctx)
                 e1.record(stream)
                 e1.synchronize()
                 if k >= 3:
                     ms.append(e0.elapsed_time(e1))
-            return statistics.median(ms), lo.cpu().numpy(), raw.cpu().numpy(), st.cpu().numpy()
+            lk.lk_plan_destroy(plan)
         finally:
             lk.lk_destroy(ctx)
-
-    out = {}
-    g = W.knit_yarn()
-    med, lo, raw, st = timed(g)
-    sizes = g.sizes()[g.pairs].prod(axis=1)
-    out["knit_yarn"] = {"loops": g.n_loops, "pairs": int(g.pairs.shape[0]), "segment_pairs": int(sizes.sum()),
-                        "ms": med, "value": float(sizes.sum()) / (med / 1e3), "unit": UNIT,
-                        "all_status_ok": bool(np.all(st == 0)),
-                        "max_abs_raw_minus_lk": float(np.max(np.abs(raw - lo)))}
-    tl = []
-    for p, q in ((2, 3), (5, 7), (11, 13), (31, 37)):
-        g = W.torus_link(p, q, 250_000, dtype=np.float32)
-        med, lo, raw, st = timed(g)
-        sps = g.segment_pairs()
-        tl.append({"p": p, "q": q, "segments_per_component": 250_000, "ms": med, "value": sps / (med / 1e3),
-                   "unit": UNIT, "lk": int(lo[0]), "closed_form_abs_lk": p * q,
-                   "abs_raw_err_vs_closed_form": float(abs(abs(raw[0]) - p * q)), "status_ok": bool(st[0] == 0)})
-    out["torus_links"] = tl
-    return out
+        res[label + "_ms"] = statistics.median(ms)
+    res["use_tuned"] = bool(res["tuned_ms"] < res["default_ms"])
+    return res, (table if res["use_tuned"] else None)
 
 
 def cpu_baseline(g):
+    """The FP64 oracle on the sheet: every pair on all host cores (one pass),
+    and a seeded 1/16 sample of the pairs on one core."""
     from oracle import oracle as O
 
     threads = O.default_threads()
     t0 = time.perf_counter()
     raw = O.link_pairs(g.vertices, g.offsets, g.pairs, threads=threads)
     dt = time.perf_counter() - t0
+    pick = np.sort(np.random.default_rng(13).choice(g.pairs.shape[0], g.pairs.shape[0] // 16, replace=False))
+    t0 = time.perf_counter()
+    O.link_pairs(g.vertices, g.offsets, g.pairs[pick], threads=1)
+    dt1 = time.perf_counter() - t0
     return raw, {"value": g.segment_pairs() / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-                 "sample": "all %d candidate pairs of the sheet, one pass (%.1f s)" % (g.pairs.shape[0], dt)}
+                 "sample": "all %d candidate pairs of the sheet, one pass (%.1f s)" % (g.pairs.shape[0], dt),
+                 "cpu": cpu_model(), "one_core": {"value": g.segment_pairs(g.pairs[pick]) / dt1, "unit": UNIT,
+                                                   "cores": 1, "sample": "%d seeded pairs (1/16 of the sheet), %.1f s"
+                                                   % (pick.size, dt1)}}
+
+
+def workload_config(g, desc):
+    return {"workload": desc, "pairs": int(g.pairs.shape[0]), "segment_pairs_per_step": int(g.segment_pairs())}
 
 
 def run_reference(args):
+    """The oracle on the headline workload: each step verifies the whole sheet
+    on all host cores when the run fits in about two minutes (the driver's
+    --steps/--warmup do), else a seeded sample of the pairs sized to fit."""
     rank, world, _ = dist_info()
     if rank != 0:
         return
@@ -419,12 +586,18 @@ def run_reference(args):
 
     g, desc = workload(0)
     threads = O.default_threads()
+    n = g.pairs.shape[0]
+    # one untimed probe of the oracle's rate sizes the per-step sample
+    probe = np.random.default_rng(1).choice(n, max(1, n // 64), replace=False)
+    t0 = time.perf_counter()
+    O.link_pairs(g.vertices, g.offsets, g.pairs[probe], threads=threads)
+    full_s = (time.perf_counter() - t0) * n / probe.size
+    frac = min(1.0, 120.0 / max(full_s * (args.steps + args.warmup), 1e-9))
+    per_step = n if frac >= 1.0 else max(1, int(n * frac))
     rng = np.random.default_rng(0)
-    per_step = max(1, g.pairs.shape[0] // 16)
     times, sps = [], []
     for s in range(args.warmup + args.steps):
-        pick = rng.choice(g.pairs.shape[0], per_step, replace=False)
-        sub = g.pairs[pick]
+        sub = g.pairs if per_step == n else g.pairs[rng.choice(n, per_step, replace=False)]
         t0 = time.perf_counter()
         O.link_pairs(g.vertices, g.offsets, sub, threads=threads)
         dt = time.perf_counter() - t0
@@ -432,12 +605,14 @@ def run_reference(args):
             times.append(dt)
             sps.append(g.segment_pairs(sub))
     value = sum(sps) / sum(times)
-    sample = "%d seeded random candidate pairs per step (1/16 of the sheet)" % per_step
+    sample = ("all %d candidate pairs of the sheet per step" % n if per_step == n else
+              "%d seeded random candidate pairs per step (of %d)" % (per_step, n))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": desc, "pairs_per_step": per_step},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": workload_config(g, desc),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -469,10 +644,17 @@ def run_ours(args):
     raw_o = torch.zeros(n, dtype=torch.float64, device=dev)
     st_o = torch.zeros(n, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+    # The autotuner's table against the built-in split; the timed run uses the faster.
+    tuning, table = tuning_block(g, v, off, pairs_d, stream, flush)
 
     opt = lk.lk_default_options()
     opt.timing = 1
     ctx = lk.lk_create(v, off, opt, stream)
+    if table is not None:
+        lk.lk_tune_set(ctx, table)
     plan = lk.lk_plan_create(ctx, pairs_d, stream)
 
     def step_timed():
@@ -516,6 +698,8 @@ def run_ours(args):
     lk_host = lk_o.cpu().numpy()
     raw_host = raw_o.cpu().numpy()
     st_host = st_o.cpu().numpy()
+    est_host = np.zeros(n)
+    lk.lk_get_error_estimates(ctx, est_host)
 
     # All-FP64 direct sum on the same GPU and workload (the baseline to beat).
     opt64 = lk.lk_default_options()
@@ -584,22 +768,25 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "precision": "FP32 segment-pair terms, FP64 accumulation, FP64 recompute of near pairs",
         "data": "synthetic",
-        "config": {"workload": desc, "pairs": int(n), "segment_pairs_per_step": int(sps_per_step),
-                   "l2": "flushed before every timed step (256 MB write)", "step": "one CUDA-graph replay"},
+        "config": workload_config(g, desc),
+        "timing": {"l2": "flushed before every timed step (256 MB write)", "step": "one CUDA-graph replay",
+                   "work_split": "autotuned" if table is not None else "built-in"},
         "p50_verify_ms": float(np.percentile(step_ms, 50)), "p99_verify_ms": float(np.percentile(step_ms, 99)),
-        "fp64_baseline": {"value": fp64_value, "unit": UNIT, "ms_per_step": statistics.median(f64_ms),
-                          "speedup_mixed_over_fp64": value / world / fp64_value,
-                          "max_abs_raw_diff_vs_mixed": float(np.max(np.abs(raw64_host - raw_host)))},
-        "fp64_recomputed_segment_pairs": stats["fp64_pairs"], "careful_items": stats["careful_items"], "careful_chunks": stats["careful_chunks"],
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": SWEEP_TRAFFIC_BYTES,
+        "fp64_recomputed_segment_pairs": stats["fp64_pairs"], "careful_items": stats["careful_items"],
+        "careful_chunks": stats["careful_chunks"],
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": SWEEP_TRAFFIC_BYTES,
                      "traffic_unit": "bytes per launch", "kernel": "sweep_packed_kernel<fast>",
                      "kernel_ms": sweep_avg, "flops_per_segment_pair": FLOPS_PER_SP,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+                     "peak_source": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz" % (
+                         n_sms, FP32_LANES_PER_SM, SM_MAX_MHZ)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": statistics.mean(e2e_ms), "results_match_device_run": e2e_ok},
         "gpu_launches": KERNELS_PER_STEP * args.steps,
-        "clocks": clk, "wall_s_timed_region": wall,
+        "clocks": clk, "wall_s_timed_region": wall, "tuning": tuning,
+        "fp64_baseline": {"value": fp64_value, "unit": UNIT, "ms_per_step": statistics.median(f64_ms),
+                          "speedup_mixed_over_fp64": value / world / fp64_value,
+                          "max_abs_raw_diff_vs_mixed": float(np.max(np.abs(raw64_host - raw_host)))},
     }
     if world == 1:
         line["one_call_per_pair"] = per_pair_block(g, v, off, lk_host, stream)
@@ -616,11 +803,60 @@ def run_ours(args):
         line["cpu_baseline"] = cb
         ref_lk = np.sign(ref_raw) * np.floor(np.abs(ref_raw) + 0.5)
         line["parity_vs_oracle"] = {"lk_bit_exact": bool(np.array_equal(lk_host, ref_lk.astype(np.int32))),
-                                    "max_abs_raw_err": float(np.max(np.abs(raw_host - ref_raw))),
+                                    "raw_err_vs_oracle": err_stats(raw_host, ref_raw),
+                                    "max_error_estimate": float(np.max(est_host)),
                                     "all_status_ok": bool(np.all(st_host == 0))}
+    line["summary"] = summary(line)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _g(x, digits=3):
+    """A number rounded to `digits` significant digits (compact JSON)."""
+    if x is None or not isinstance(x, (int, float)) or x == 0 or not np.isfinite(x):
+        return x
+    return float("%.*g" % (digits, x))
+
+
+def summary(line):
+    """The numbers the tail of the line must hold: the FP64 baseline, serving,
+    every configuration's rate and its worst raw error against the oracle or
+    the closed form."""
+    out = {"fp64_gpu": {"sp_s": _g(line["fp64_baseline"]["value"]),
+                        "mixed_speedup": _g(line["fp64_baseline"]["speedup_mixed_over_fp64"])},
+           "roofline_frac": _g(line["roofline"]["frac"]), "e2e_sp_s": _g(line["e2e"]["value"])}
+    err, rate = {}, {}
+    if "parity_vs_oracle" in line:
+        err["chainmail"] = _g(line["parity_vs_oracle"]["raw_err_vs_oracle"]["max"])
+    if "serving" in line:
+        sv = line["serving"]
+        out["serving"] = {"cap_req_s": _g(sv["capacity"]["req_per_s"]), "cap_sp_s": _g(sv["capacity"]["sp_per_s"]),
+                          "n_req": sv["loads"][0]["n_requests"],
+                          "p50_ms": [_g(x["p50_ms"]) for x in sv["loads"]],
+                          "p99_ms": [_g(x["p99_ms"]) for x in sv["loads"]]}
+    if "configs" in line:
+        c = line["configs"]
+        err["ring_chain"] = _g(c["ring_chain"]["raw_err_vs_oracle"]["max"])
+        err["knit_sample"] = _g(c["knit_yarn"]["raw_err_vs_oracle"]["max"])
+        rate["ring_chain"] = _g(c["ring_chain"]["value"])
+        rate["knit"] = _g(c["knit_yarn"]["value"])
+        rate["knit_fp64"] = _g(c["knit_yarn"]["fp64_gpu"]["value"])
+        for t in c["torus_links"]["links"]:
+            key = "torus%d_%d_%dk" % (t["p"], t["q"], t["segments_per_component"] // 1000)
+            err[key] = _g(t["abs_raw_err_vs_closed_form"])
+            rate[key] = _g(t["value"])
+        rate["torus_fp64"] = _g(c["torus_links"]["fp64_gpu_rate"]["value"])
+    if "stress" in line:
+        for k, rec in line["stress"].items():
+            err[k] = _g(rec["direct_sum"]["max_abs_raw_err"])
+            rate[k] = _g(rec["direct_sum"]["value"])
+    if "cpu_baseline" in line:
+        out["oracle_sp_s"] = {"cores": line["cpu_baseline"]["cores"], "all": _g(line["cpu_baseline"]["value"]),
+                              "one": _g(line["cpu_baseline"]["one_core"]["value"])}
+    out["sp_s"] = rate
+    out["max_raw_err"] = err
+    return out
 
 
 def main():

@@ -57,8 +57,8 @@ typedef enum {
     /* FP32 bulk sweep with FP64 accumulation; segment pairs closer than
      * near_ratio segment lengths are recomputed in FP64. */
     LK_MIXED = 0,
-    /* every segment pair in FP64 with two atan2 per pair (Algorithm 5 as
-     * written): the plain all-FP64 GPU direct sum. */
+    /* every segment pair's term of Eq. 4 in FP64 with two atan2 (one per
+     * triangle of the cell): the plain all-FP64 GPU direct sum. */
     LK_ALL_F64 = 1
 } lk_precision;
 
@@ -119,6 +119,15 @@ typedef struct lk_options {
     int cc_capacity;     /* LK_METHOD_CC: candidate crossings per verify (default 1<<18); pairs
                             whose candidates do not fit are computed by the direct sum */
     int cc_search;       /* lk_cc_search, default LK_CC_SEARCH_AUTO */
+    double precise_tol;  /* LK_MIXED: the bulk sweep records its rounding-error statistics, and a
+                            pair of the accurate variant whose estimated error of raw (see
+                            lk_get_error_estimates) exceeds precise_tol has its bulk sum formed
+                            again with compensated FP32 arithmetic (every quantity an unevaluated
+                            sum of two floats, errors near 1e-10 where FP32 terms reach 1e-5; about
+                            6 times the accurate variant's work), in the same call.  0 = never;
+                            default 1e-7, a tenth of the 1e-6 raw tolerance.  Such pairs' vertices
+                            (those of every accurate-variant pair) are staged on a 2^-22 grid of
+                            the pair's frame so that vertex differences are exact. */
 } lk_options;
 
 typedef struct lk_stats {
@@ -134,6 +143,7 @@ typedef struct lk_stats {
     int64_t careful_chunks;   /* 32-row chunks swept again with per-pair tests */
     int64_t cc_candidates;    /* LK_METHOD_CC: candidate crossings found by the FP32 search */
     int64_t cc_fallback_pairs;/* LK_METHOD_CC: pairs the crossings could not decide (direct sum) */
+    int64_t precise_pairs;    /* pairs summed again by the compensated sweep (options.precise_tol) */
 } lk_stats;
 
 typedef struct lk_ctx lk_ctx;
@@ -224,6 +234,27 @@ lk_status lk_sync(lk_ctx* ctx, void* cuda_stream);
 /* Statistics of the most recent completed verify or plan run on this context. */
 lk_status lk_get_stats(lk_ctx* ctx, lk_stats* out);
 
+/*
+ * Per-pair error estimates of the last verify or plan run on this context
+ * (LK_MIXED): an estimate of |raw - exact| in units of the linking number,
+ * where "exact" is the direct sum of the same staged polylines in exact
+ * arithmetic (the integer linking number).  It is 4 standard deviations of
+ * the bulk sweep's rounding errors (each work item records the sum of its
+ * chunk columns' squared angles and a per-cell scale L^2/m^2: longest
+ * segment over nearest grid distance), plus the part that a rounded |s|^2
+ * shared by a whole row or column adds coherently, plus, for pairs of the
+ * fast variant, 1e-8 times the summed |angle| for the bias of the hardware
+ * approximations.  Segment pairs summed by the careful pass or in FP64 are
+ * not included; pairs decided by counting crossings have 0; a pair whose
+ * status is not LK_OK has NaN.  The estimate is not a bound.
+ *  err_out : [n_pairs] double, host or device, in the order of the verify's
+ *            pair list; n_pairs must equal that list's length.
+ * Ordered on cuda_stream after the verify; returns after the copy when
+ * err_out is host memory.  Errors: LK_ERR_ARG (no such verify, wrong
+ * n_pairs, LK_ALL_F64), LK_ERR_CUDA.
+ */
+lk_status lk_get_error_estimates(const lk_ctx* ctx, double* err_out, int64_t n_pairs, void* cuda_stream);
+
 /* The options the context runs with: those given to lk_create, with the
  * list sizes as grown by later verifies.  Errors: LK_ERR_ARG. */
 lk_status lk_get_options(const lk_ctx* ctx, lk_options* out);
@@ -254,17 +285,26 @@ void lk_plan_destroy(lk_plan* plan);
 
 /*
  * Early-exit verification of a certificate (Sec. 3.1, "Fast Verification":
- * exit as soon as any linking number differs from the input).  Verifies the
- * pairs in input order, in batches of at most batch_segment_pairs segment
- * pairs (0 = 2^30; every batch holds at least one pair), and after each batch
- * compares the rounded linking numbers with expected[] ([n_pairs] int32, host
- * or device).  A pair whose status is not LK_OK also counts as a mismatch.
+ * exit as soon as any linking number differs from the input; Algorithm 1's
+ * comparison of M_0 with M_t).  The pairs are verified in input order, in
+ * batches of at most batch_segment_pairs segment pairs (0 = 2^28; every batch
+ * holds at least one pair), all enqueued on cuda_stream back to back with no
+ * host round trip between them.  expected[] ([n_pairs] int32, host or device)
+ * is copied to the device; after each batch a kernel compares its rounded
+ * linking numbers with it and records the first index that differs (a pair
+ * whose status is not LK_OK also counts) in a device word.  Every kernel of
+ * the later batches reads that word first -- the persistent sweeps before
+ * each work item they take -- and does nothing once it is set, so the work
+ * after the first differing batch costs only its launches.  No kernel waits
+ * on the word.
  *  *first_mismatch : the smallest mismatching index of the first batch that
  *                    has one, or -1 if every pair matches.
- *  *n_checked      : pairs verified before stopping (a prefix of the list).
+ *  *n_checked      : pairs verified before stopping (a prefix of the list:
+ *                    up to the end of the batch holding the mismatch).
  * lk_out / raw_out / status_out (may be NULL) receive the results of the
  * checked prefix; entries past it are left untouched.  Synchronises
- * cuda_stream after each batch.  Errors: as lk_verify.
+ * cuda_stream once, at the end.  Device memory: 20 bytes per pair, plus the
+ * work buffers of the largest batch.  Errors: as lk_verify.
  */
 lk_status lk_verify_expected(lk_ctx* ctx, const int32_t* loop_pairs, const int32_t* expected,
                              int64_t n_pairs, int64_t batch_segment_pairs, int64_t* first_mismatch,
@@ -374,16 +414,22 @@ void lk_server_destroy(lk_server* srv);
  * whose memory pool already owns all of device memory, or a host program that
  * forbids libraries to call cudaMalloc.  It runs the same kernels as
  * lk_verify with the default options, but every work buffer lives in one
- * file-scope device array of 32 MiB that each GPU loading the library holds
+ * file-scope device array of 48 MiB that each GPU loading the library holds
  * until the process exits; it calls no cudaMalloc, cudaFree or allocating
  * library routine.
  *  vertices     : [n_vertices][3] of vdtype, host or device memory.
  *  loop_offsets : [n_loops+1] int64, HOST memory (CSR as for lk_create).
  *  loop_pairs   : [n_pairs][2] int32, HOST memory.
  *  lk_out, raw_out, status_out : as for lk_verify (host or device, may be NULL).
- * Limits: n_vertices <= 262144, n_loops <= 16384, n_pairs <= 16384 and at most
- * 262144 work items (tiles of 128 x tile_rows segment pairs); larger inputs
- * return LK_ERR_ARG with a message naming the limit, before any device work.
+ * Limits: n_vertices <= 262144, n_loops <= 16384, n_pairs <= 16384, at most
+ * 262144 work items (tiles of 128 x tile_rows segment pairs) and at most 2^23
+ * 32-row chunk slots in the items of pairs of at least accurate_threshold
+ * segment pairs; larger inputs return LK_ERR_ARG with a message naming the
+ * limit, before any device work.  The chunk hand-over list holds 65536
+ * chunks: a call with more chunks near enough for the careful pass hands
+ * whole work items to it instead (the results are unchanged, only slower),
+ * and its FP64 recompute list holds 65536 segment pairs (the rest are
+ * evaluated in place).  None of these buffers ever grows.
  * The first call on each device looks up the array's device address once
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call on a device shares the one array and leaves its contents behind

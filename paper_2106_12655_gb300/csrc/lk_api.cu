@@ -55,8 +55,10 @@ template <class T>
 struct DevBuf {
     T* p = nullptr;
     size_t cap = 0;  // elements
+    bool fixed = false;  // bound to memory the buffer does not own (never freed or reallocated)
     cudaError_t ensure(size_t n) {
         if (n <= cap && p) return cudaSuccess;
+        if (fixed) return cudaErrorInvalidValue;   // callers check fits() first
         if (p) cudaFree(p);
         p = nullptr;
         cap = 0;
@@ -65,13 +67,17 @@ struct DevBuf {
         if (e == cudaSuccess) cap = want;
         return e;
     }
+    bool fits(size_t n) const { return !fixed || (p && n <= cap); }
     void release() {
-        if (p) cudaFree(p);
+        if (p && !fixed) cudaFree(p);
         p = nullptr;
         cap = 0;
     }
     size_t bytes_for(size_t n) const { return std::max<size_t>(n, 1) * sizeof(T); }
 };
+
+// Work counters of a verify (see Workspace::counters).
+constexpr size_t kCounters = 12;
 
 // A counting-crossings pair searched with the binned candidate search.
 struct GridJob {
@@ -95,6 +101,7 @@ struct Packed {
     int64_t n_acc_items = 0;   // items [0, n_acc_items) belong to accurate-variant pairs
     int64_t n_acc_tasks = 0;   // and tasks [0, n_acc_tasks)
     int64_t n_chunks = 0;      // 32-row chunks over all items
+    int64_t n_chunk_bits = 0;  // chunk bits of the accurate-variant items (PairTask::bit_base)
     int64_t segment_pairs = 0;
     int tile_rows_max = 0;
     int tile_cols = 0;
@@ -116,8 +123,8 @@ struct Workspace {
     DevBuf<unsigned long long> counters;  // [0] accurate-sweep counter, [1] overflow,
                                           // [2] u32 careful_count, careful_counter,
                                           // [3] u32 near_count, unused, [4] fast-sweep / f64 counter,
-                                          // [5], [6] chunk pass, [8] crossing sweep counter,
-                                          // [9] u32 crossing candidates
+                                          // [5], [6] chunk pass, [7] precise sweep, [8] crossing sweep
+                                          // counter, [9] u32 crossing candidates, [10] precise careful pass
     DevBuf<NearEntry> cc_list;            // counting crossings: candidates (method CC only)
     DevBuf<int> cc_half;
     DevBuf<unsigned int> flag_scan, flag_sums;   // counting crossings: items of the undecided pairs
@@ -128,6 +135,10 @@ struct Workspace {
     DevBuf<int32_t> lk;
     DevBuf<double> raw;
     DevBuf<int32_t> status;
+    DevBuf<float4> item_err;              // bulk-sweep error statistics per item
+    DevBuf<unsigned int> chunk_bits;      // chunks the careful pass sums (accurate variant)
+    DevBuf<unsigned int> precise_scan, precise_sums;   // items of the kFlagPrecise pairs
+    DevBuf<double> err;                   // per-pair error estimates, by output position
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the bulk sweep (options.timing)
 
     cudaError_t events() {
@@ -147,6 +158,7 @@ struct Workspace {
         cc_list.release(); cc_half.release(); flag_scan.release(); flag_sums.release();
         grid_offsets.release(); grid_cursor.release(); grid_sums.release(); grid_entries.release();
         grid_row_xy.release(); grid_col_xy.release(); grid_meta.release();
+        item_err.release(); chunk_bits.release(); precise_scan.release(); precise_sums.release(); err.release();
     }
 };
 
@@ -175,6 +187,8 @@ struct lk_ctx {
     const unsigned long long* stats_overflow = nullptr;
     const unsigned int* stats_careful = nullptr;
     const int* stats_flags = nullptr;            // per-pair flags of the last verify (CC fallbacks)
+    const double* last_err = nullptr;            // the last verify's per-pair error estimates
+    int64_t last_n = 0;
     bool stats_cc = false;
     cudaEvent_t stats_ev0 = nullptr, stats_ev1 = nullptr;
     cudaStream_t stats_stream = nullptr;
@@ -194,6 +208,11 @@ struct lk_ctx {
     // List growth: after each lk_verify its work counters are copied to pinned
     // host memory on the stream; a later lk_verify reads them once the copy has
     // landed (without waiting for it) and enlarges any list that overflowed.
+    // Early exit (lk_verify_expected): the certificate, the stop word and the
+    // results of every batch, on the device.
+    DevBuf<int32_t> ee_expected, ee_lk, ee_status;
+    DevBuf<double> ee_raw;
+    DevBuf<long long> ee_stop;
     unsigned long long* h_counters = nullptr;   // [10], pinned
     cudaEvent_t counters_ev = nullptr;
     bool counters_pending = false;
@@ -413,6 +432,7 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
     pk.n_acc_items = 0;
     pk.n_acc_tasks = 0;
     pk.n_chunks = 0;
+    pk.n_chunk_bits = 0;
     for (int64_t k = 0; k < n; ++k) {
         const int64_t p = order[(size_t)k];
         const Shape& q = sh[(size_t)p];
@@ -432,6 +452,12 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
             t.tile_rows = q.tile_rows;
             t.col_tiles = q.col_tiles;
             t.accurate = q.accurate;
+            if (q.accurate) {
+                // one bit per chunk slot of each item (the precise sweep skips the
+                // chunks the bulk sweep handed to the careful pass)
+                t.bit_base = pk.n_chunk_bits;
+                pk.n_chunk_bits += q.items * ((q.tile_rows + lk::kChunkRows - 1) / lk::kChunkRows);
+            }
             const bool cc = ctx->opt.method == LK_METHOD_CC;
             const int search = ctx->opt.cc_search;
             const bool fits = q.n_rows <= lk::kCcLocalMax && q.n_cols <= lk::kCcLocalMax;
@@ -496,7 +522,10 @@ size_t grid_bytes(const Packed* pk) {
 size_t workspace_bytes(const lk_ctx* ctx, int64_t n_tasks, int64_t n_items, int64_t n_chunks, const Packed* pk) {
     const size_t near = (size_t)std::max(0, ctx->opt.near_capacity);
     const size_t cc = ctx->opt.method == LK_METHOD_CC ? (size_t)std::max(1, ctx->opt.cc_capacity) : 0;
-    return n_tasks * (sizeof(PairTask) + 8 + 8 + 8 + 4 + 4 + 8 + 4 + (cc ? 4 + 4 : 0)) + n_items * (4 + 8 + 8 + 8) +
+    const size_t stats = ctx->opt.precision != LK_ALL_F64 ? 1 : 0;
+    const size_t bits = pk ? (size_t)(pk->n_chunk_bits + 31) / 32 * 4 : 0;
+    return n_tasks * (sizeof(PairTask) + 8 + 8 + 8 + 4 + 4 + 8 + 4 + (cc ? 4 + 4 : 0) + stats * (4 + 8)) +
+           n_items * (4 + 8 + 8 + 8 + stats * sizeof(float4)) + bits +
            chunk_capacity(ctx->opt, n_chunks) * sizeof(lk::CarefulChunk) +
            (near + cc) * sizeof(NearEntry) + grid_bytes(pk) + 80;
 }
@@ -513,6 +542,19 @@ lk_status ensure_workspace(lk_ctx* ctx, Workspace& ws, int64_t n_tasks, int64_t 
     if (ctx->opt.mem_budget > 0 && workspace_bytes(ctx, n_tasks, n_items, n_chunks, pk) > ctx->opt.mem_budget)
         return fail(ctx, LK_ERR_OOM, "lk_verify: work buffers exceed mem_budget");
     const size_t nt = (size_t)std::max<int64_t>(n_tasks, 1), ni = (size_t)std::max<int64_t>(n_items, 1);
+    // Buffers bound to fixed memory (the allocation-free entry point) are never
+    // reallocated: a need beyond one of them is an argument error.
+    const size_t bit_words = pk ? (size_t)std::max<int64_t>((pk->n_chunk_bits + 31) / 32, 1) : 1;
+    const bool stats = ctx->opt.precision != LK_ALL_F64;
+    if (!ws.tasks.fits(nt) || !ws.item_begin.fits(nt + 1) || !ws.item_task.fits(ni) || !ws.partial.fits(ni) ||
+        !ws.careful_items.fits(ni) || !ws.careful_chunks.fits(chunk_capacity(ctx->opt, n_chunks)) ||
+        !ws.item_fix.fits(ni) || !ws.near_list.fits((size_t)std::max(1, ctx->opt.near_capacity)) ||
+        !ws.fix_acc.fits(nt) || !ws.fp64_count.fits(nt) || !ws.flags.fits(nt) || !ws.lk.fits(nt) ||
+        !ws.counters.fits(kCounters) ||
+        !ws.raw.fits(nt) || !ws.status.fits(nt) ||
+        (stats && (!ws.item_err.fits(ni) || !ws.chunk_bits.fits(bit_words) || !ws.precise_scan.fits(nt + 1) ||
+                   !ws.precise_sums.fits(nt / 4096 + 2) || !ws.err.fits(nt))))
+        return fail(ctx, LK_ERR_ARG, "lk_verify: work beyond the fixed buffers' limits");
     LK_CUDA(ctx, ws.tasks.ensure(nt));
     LK_CUDA(ctx, ws.item_begin.ensure(nt + 1));
     LK_CUDA(ctx, ws.item_task.ensure(ni));
@@ -524,7 +566,7 @@ lk_status ensure_workspace(lk_ctx* ctx, Workspace& ws, int64_t n_tasks, int64_t 
     LK_CUDA(ctx, ws.fix_acc.ensure(nt));
     LK_CUDA(ctx, ws.fp64_count.ensure(nt));
     LK_CUDA(ctx, ws.flags.ensure(nt));
-    LK_CUDA(ctx, ws.counters.ensure(10));
+    LK_CUDA(ctx, ws.counters.ensure(kCounters));
     if (ctx->opt.method == LK_METHOD_CC) {
         LK_CUDA(ctx, ws.cc_list.ensure((size_t)std::max(1, ctx->opt.cc_capacity)));
         LK_CUDA(ctx, ws.cc_half.ensure(nt));
@@ -543,6 +585,13 @@ lk_status ensure_workspace(lk_ctx* ctx, Workspace& ws, int64_t n_tasks, int64_t 
     LK_CUDA(ctx, ws.lk.ensure(nt));
     LK_CUDA(ctx, ws.raw.ensure(nt));
     LK_CUDA(ctx, ws.status.ensure(nt));
+    if (stats) {
+        LK_CUDA(ctx, ws.item_err.ensure(ni));
+        LK_CUDA(ctx, ws.chunk_bits.ensure(bit_words));
+        LK_CUDA(ctx, ws.precise_scan.ensure(nt + 1));
+        LK_CUDA(ctx, ws.precise_sums.ensure(nt / 4096 + 2));
+        LK_CUDA(ctx, ws.err.ensure(nt));
+    }
     if (ctx->opt.timing) LK_CUDA(ctx, ws.events());
     return LK_OK;
 }
@@ -593,6 +642,11 @@ lk::SweepArgs sweep_args(const lk_ctx* ctx, Workspace& ws, const Packed& pk) {
         a.cc_half = ws.cc_half.p;
         a.flag_scan = ws.flag_scan.p;
     }
+    if (ctx->opt.precision != LK_ALL_F64) {
+        a.item_err = ws.item_err.p;
+        a.chunk_bits = pk.n_chunk_bits > 0 ? ws.chunk_bits.p : nullptr;
+        a.precise_scan = ws.precise_scan.p;
+    }
     return a;
 }
 
@@ -606,11 +660,14 @@ cudaError_t record_event(cudaEvent_t ev, cudaStream_t s) {
                                                 : cudaEventRecord(ev, s);
 }
 
-// The device sequence of one verify (graph-capturable: no host sync).
-lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStream_t s) {
+// The device sequence of one verify (graph-capturable: no host sync).  With
+// `stop` set (early exit), every kernel first reads *stop and does nothing
+// when it is below stop_base.
+lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStream_t s,
+                         const long long* stop = nullptr, long long stop_base = 0) {
     const int64_t n = (int64_t)pk.tasks.size();
     if (n == 0) return LK_OK;
-    LK_CUDA(ctx, cudaMemsetAsync(ws.counters.p, 0, 10 * sizeof(unsigned long long), s));
+    LK_CUDA(ctx, cudaMemsetAsync(ws.counters.p, 0, kCounters * sizeof(unsigned long long), s));
     LK_CUDA(ctx, cudaMemsetAsync(ws.fix_acc.p, 0, n * sizeof(unsigned long long), s));
     const bool cc = ctx->opt.method == LK_METHOD_CC;
     if (cc) LK_CUDA(ctx, cudaMemsetAsync(ws.cc_half.p, 0, n * sizeof(int), s));
@@ -618,8 +675,30 @@ lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStrea
     LK_CUDA(ctx, cudaMemsetAsync(ws.flags.p, 0, n * sizeof(int), s));
     if (pk.n_items > 0)
         LK_CUDA(ctx, cudaMemsetAsync(ws.item_fix.p, 0, pk.n_items * sizeof(unsigned long long), s));
+    const bool mixed = ctx->opt.precision != LK_ALL_F64;
+    if (mixed && pk.n_chunk_bits > 0)
+        LK_CUDA(ctx, cudaMemsetAsync(ws.chunk_bits.p, 0, (size_t)(pk.n_chunk_bits + 31) / 32 * sizeof(unsigned int), s));
     lk::launch_pair_frames(ws.tasks.p, n, ctx->d_aabb, s);
-    const lk::SweepArgs a = sweep_args(ctx, ws, pk);
+    lk::SweepArgs a = sweep_args(ctx, ws, pk);
+    a.stop = stop;
+    a.stop_base = stop_base;
+    lk::ReduceArgs r{};
+    r.tasks = ws.tasks.p;
+    r.item_err = mixed ? ws.item_err.p : nullptr;
+    r.err_out = mixed ? ws.err.p : nullptr;
+    r.stop = stop;
+    r.stop_base = stop_base;
+    r.cc_half = cc ? ws.cc_half.p : nullptr;
+    r.item_begin = ws.item_begin.p;
+    r.partial = ws.partial.p;
+    r.fix_acc = ws.fix_acc.p;
+    r.item_fix = ctx->opt.precision == LK_ALL_F64 ? nullptr : ws.item_fix.p;
+    r.flags = ws.flags.p;
+    r.n_tasks = n;
+    r.int_tol = ctx->opt.int_tol;
+    r.lk_out = ws.lk.p;
+    r.raw_out = ws.raw.p;
+    r.status_out = ws.status.p;
     if (pk.n_items > 0) {
         if (ctx->opt.precision == LK_ALL_F64) {
             const int grid = ctx->num_sms * lk::sweep_f64_blocks_per_sm();
@@ -637,7 +716,7 @@ lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStrea
                     int G = 1;
                     while (G < lk::kCcLocalGridMax && G * G < pk.local_rows) G <<= 1;
                     const lk::CcLocalShape S{pk.local_rows, pk.local_cols, G, lk::kCcLocalEntries * pk.local_rows};
-                    lk::launch_cc_local(a, n, S, s);
+                    LK_CUDA(ctx, lk::launch_cc_local(a, n, pk.n_cc_local, S, s));
                 }
                 if (!pk.grid.empty()) {
                     const lk::CcGridWork w{ws.grid_offsets.p, ws.grid_cursor.p, ws.grid_sums.p, ws.grid_entries.p,
@@ -645,7 +724,7 @@ lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStrea
                                            ws.grid_row_xy.p, ws.grid_col_xy.p,
                                            reinterpret_cast<int*>(ws.grid_meta.p + 1), ws.grid_meta.p};
                     for (const GridJob& gj : pk.grid)
-                        lk::launch_cc_grid(a, gj.task, gj.n_rows, gj.n_cols, gj.G_max, w, s);
+                        LK_CUDA(ctx, lk::launch_cc_grid(a, gj.task, gj.n_rows, gj.n_cols, gj.G_max, w, s));
                 }
                 lk::launch_cc_resolve(a, ctx->num_sms * 4, s);
             }
@@ -656,24 +735,26 @@ lk_status enqueue_verify(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStrea
                                    ctx->num_sms * lk::sweep_mixed_blocks_per_sm(false), s);
             if (ctx->opt.timing) LK_CUDA(ctx, record_event(ws.ev1, s));
             const bool fast = pk.n_items > pk.n_acc_items, acc = pk.n_acc_items > 0;
+            // Pairs of the accurate variant whose estimated error (from the
+            // bulk sweep's statistics) exceeds precise_tol are flagged
+            // kFlagPrecise by a first reduction; their bulk chunks are summed
+            // again by the precise sweep and their handed-over chunks by the
+            // precise careful pass.  The final reduction replaces its results.
+            const bool precise = acc && ctx->opt.precise_tol > 0.0;
+            const int pgrid = ctx->num_sms * lk::sweep_precise_blocks_per_sm();
+            if (precise) {
+                r.precise_tol = ctx->opt.precise_tol;
+                lk::launch_reduce(r, s);
+                r.precise_tol = 0.0;
+                lk::launch_flag_scan(a, lk::kFlagPrecise, ws.precise_scan.p, ws.precise_sums.p, s);
+                lk::launch_sweep_precise(a, 0, pk.n_acc_tasks, ws.counters.p + 7, pgrid, s);
+            }
             lk::launch_careful_chunks(a, fast, acc, ctx->num_sms * lk::careful_chunk_blocks_per_sm(), s);
+            if (precise) lk::launch_precise_careful(a, ws.counters.p + 10, pgrid, s);
             lk::launch_sweep_careful(a, fast, acc, ctx->num_sms * lk::sweep_careful_blocks_per_sm(), s);
             lk::launch_near_fix(a, ctx->num_sms * 4, s);
         }
     }
-    lk::ReduceArgs r{};
-    r.tasks = ws.tasks.p;
-    r.cc_half = cc ? ws.cc_half.p : nullptr;
-    r.item_begin = ws.item_begin.p;
-    r.partial = ws.partial.p;
-    r.fix_acc = ws.fix_acc.p;
-    r.item_fix = ctx->opt.precision == LK_ALL_F64 ? nullptr : ws.item_fix.p;
-    r.flags = ws.flags.p;
-    r.n_tasks = n;
-    r.int_tol = ctx->opt.int_tol;
-    r.lk_out = ws.lk.p;
-    r.raw_out = ws.raw.p;
-    r.status_out = ws.status.p;
     lk::launch_reduce(r, s);
     LK_CUDA(ctx, cudaGetLastError());
     return LK_OK;
@@ -710,6 +791,8 @@ void note_stats(lk_ctx* ctx, Workspace& ws, const Packed& pk, cudaStream_t s) {
     ctx->stats_overflow = ws.counters.p + 1;
     ctx->stats_careful = reinterpret_cast<const unsigned int*>(ws.counters.p + 2);
     ctx->stats_flags = ws.flags.p;
+    ctx->last_err = ws.err.p;
+    ctx->last_n = (int64_t)pk.tasks.size();
     ctx->stats_cc = ctx->opt.method == LK_METHOD_CC && ws.cc_list.p != nullptr;
     ctx->stats_ev0 = (ctx->opt.timing && pk.n_items > 0) ? ws.ev0 : nullptr;
     ctx->stats_ev1 = ws.ev1;
@@ -750,6 +833,7 @@ void lk_default_options(lk_options* opt) {
     opt->method = LK_METHOD_DS;
     opt->cc_capacity = 1 << 18;
     opt->cc_search = LK_CC_SEARCH_AUTO;
+    opt->precise_tol = 1e-7;
 }
 
 const char* lk_last_error(const lk_ctx* ctx) {
@@ -773,7 +857,7 @@ lk_status lk_create(lk_ctx** out, const void* vertices, lk_dtype vdtype, int64_t
         (o.precision != LK_MIXED && o.precision != LK_ALL_F64) || o.tile_rows < 0 ||
         o.near_capacity < 1 || o.accurate_threshold < 0 || o.chunk_capacity < 1 ||
         (o.method != LK_METHOD_DS && o.method != LK_METHOD_CC) || o.cc_capacity < 1 ||
-        o.cc_search < LK_CC_SEARCH_AUTO || o.cc_search > LK_CC_SEARCH_BINNED ||
+        o.cc_search < LK_CC_SEARCH_AUTO || o.cc_search > LK_CC_SEARCH_BINNED || !(o.precise_tol >= 0.0) ||
         (o.method == LK_METHOD_CC && o.precision != LK_MIXED))
         return fail(nullptr, LK_ERR_ARG,
                     "lk_create: invalid options (near_ratio >= 3, 0 < int_tol < 0.5; LK_METHOD_CC needs LK_MIXED)");
@@ -1031,14 +1115,17 @@ lk_status lk_get_stats(lk_ctx* ctx, lk_stats* out) {
         ctx->stats.careful_chunks = u32[6];
         ctx->stats.cc_candidates = 0;
         ctx->stats.cc_fallback_pairs = 0;
-        if (ctx->stats_cc) {
-            ctx->stats.cc_candidates = (int64_t)(u32[14] | ((unsigned long long)u32[15] << 32));   // counters[9]
+        ctx->stats.precise_pairs = 0;
+        if (ctx->stats_cc) ctx->stats.cc_candidates = (int64_t)(u32[14] | ((unsigned long long)u32[15] << 32));   // counters[9]
+        {
             std::vector<int> fl((size_t)std::max<int64_t>(ctx->stats_tasks, 1), 0);
             if (ctx->stats_tasks > 0)
                 LK_CUDA(ctx, cudaMemcpy(fl.data(), ctx->stats_flags, ctx->stats_tasks * sizeof(int),
                                         cudaMemcpyDeviceToHost));
-            for (int64_t t = 0; t < ctx->stats_tasks; ++t)
-                ctx->stats.cc_fallback_pairs += (fl[(size_t)t] & lk::kFlagCcFallback) ? 1 : 0;
+            for (int64_t t = 0; t < ctx->stats_tasks; ++t) {
+                if (ctx->stats_cc) ctx->stats.cc_fallback_pairs += (fl[(size_t)t] & lk::kFlagCcFallback) ? 1 : 0;
+                ctx->stats.precise_pairs += (fl[(size_t)t] & lk::kFlagPrecise) ? 1 : 0;
+            }
         }
         ctx->stats.sweep_ms = -1.0;
         if (ctx->stats_ev0) {
@@ -1052,10 +1139,24 @@ lk_status lk_get_stats(lk_ctx* ctx, lk_stats* out) {
     return LK_OK;
 }
 
+lk_status lk_get_error_estimates(const lk_ctx* ctx, double* err_out, int64_t n_pairs, void* cuda_stream) {
+    if (!ctx || !err_out) return fail(nullptr, LK_ERR_ARG, "lk_get_error_estimates: NULL argument");
+    lk_ctx* c = const_cast<lk_ctx*>(ctx);
+    if (!ctx->last_err || n_pairs != ctx->last_n)
+        return fail(c, LK_ERR_ARG, "lk_get_error_estimates: n_pairs must equal the last verify's pair count "
+                                   "(and the last verify must have used LK_MIXED)");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    LK_CUDA(c, cudaMemcpyAsync(err_out, ctx->last_err, (size_t)n_pairs * sizeof(double), cudaMemcpyDefault, s));
+    if (!is_device_ptr(err_out)) LK_CUDA(c, cudaStreamSynchronize(s));
+    return LK_OK;
+}
+
 void lk_destroy(lk_ctx* ctx) {
     if (!ctx) return;
     drop_repeat_plan(ctx);
     ctx->ws.release();
+    ctx->ee_expected.release(); ctx->ee_lk.release(); ctx->ee_status.release(); ctx->ee_raw.release();
+    ctx->ee_stop.release();
     if (ctx->d_V) cudaFree(ctx->d_V);
     if (ctx->d_offsets) cudaFree(ctx->d_offsets);
     if (ctx->d_aabb) cudaFree(ctx->d_aabb);
@@ -1133,6 +1234,7 @@ void lk_plan_destroy(lk_plan* plan) {
     if (plan->graph) cudaGraphDestroy(plan->graph);
     if (plan->capture) cudaStreamDestroy(plan->capture);
     if (plan->ctx && plan->ctx->stats_fp64 == plan->ws.fp64_count.p) plan->ctx->stats_pending = false;
+    if (plan->ctx && plan->ctx->last_err == plan->ws.err.p) plan->ctx->last_err = nullptr;
     plan->ws.release();
     delete plan;
 }
@@ -1154,13 +1256,14 @@ void lk_plan_destroy(lk_plan* plan) {
 // no cudaMalloc, cudaFree or allocating library routine.
 namespace {
 
-constexpr size_t kNoallocScratchBytes = (size_t)32 << 20;   // 32 MiB per device, held until exit
+constexpr size_t kNoallocScratchBytes = (size_t)48 << 20;   // 48 MiB per device, held until exit
 constexpr int64_t kNoallocMaxVertices = (int64_t)1 << 18;
 constexpr int64_t kNoallocMaxLoops = (int64_t)1 << 14;
 constexpr int64_t kNoallocMaxPairs = (int64_t)1 << 14;
 constexpr int64_t kNoallocMaxItems = (int64_t)1 << 18;
 constexpr int kNoallocNearCapacity = 1 << 16;
-constexpr int64_t kNoallocMaxChunks = (int64_t)1 << 16;
+constexpr int64_t kNoallocMaxChunks = (int64_t)1 << 16;     // chunk hand-over list entries
+constexpr int64_t kNoallocMaxChunkBits = (int64_t)1 << 23;  // chunk slots of accurate-variant items
 constexpr int kNoallocMaxDevices = 64;
 
 std::mutex g_noalloc_mu;
@@ -1244,6 +1347,9 @@ extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, in
     lk_ctx ctx;
     lk_default_options(&ctx.opt);
     ctx.opt.near_capacity = kNoallocNearCapacity;
+    // the hand-over list holds what the scratch reserves; a batch with more
+    // chunks to hand over passes whole items to the careful pass instead
+    ctx.opt.chunk_capacity = (int)kNoallocMaxChunks;
     ctx.n_vertices = n_vertices;
     ctx.n_loops = n_loops;
     ctx.h_offsets.assign(loop_offsets, loop_offsets + n_loops + 1);
@@ -1262,6 +1368,7 @@ extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, in
         using T = typename std::remove_pointer<decltype(buf.p)>::type;
         buf.p = L.take<T>(count);
         buf.cap = count;
+        buf.fixed = true;
     };
     bind(ws.tasks, (size_t)kNoallocMaxPairs);
     bind(ws.item_begin, (size_t)kNoallocMaxPairs + 1);
@@ -1274,17 +1381,24 @@ extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, in
     bind(ws.fix_acc, (size_t)kNoallocMaxPairs);
     bind(ws.fp64_count, (size_t)kNoallocMaxPairs);
     bind(ws.flags, (size_t)kNoallocMaxPairs);
-    bind(ws.counters, 10);
+    bind(ws.counters, kCounters);
     bind(ws.lk, (size_t)kNoallocMaxPairs);
     bind(ws.raw, (size_t)kNoallocMaxPairs);
     bind(ws.status, (size_t)kNoallocMaxPairs);
+    bind(ws.item_err, (size_t)kNoallocMaxItems);
+    bind(ws.chunk_bits, (size_t)kNoallocMaxChunkBits / 32);
+    bind(ws.precise_scan, (size_t)kNoallocMaxPairs + 1);
+    bind(ws.precise_sums, (size_t)kNoallocMaxPairs / 4096 + 2);
+    bind(ws.err, (size_t)kNoallocMaxPairs);
     if (L.off > kNoallocScratchBytes) return fail(nullptr, LK_ERR_ARG, "lk_verify_noalloc: scratch layout overflow");
 
     Packed pk;
     if ((st = pack_pairs(&ctx, loop_pairs, n_pairs, pk)) != LK_OK) return fail(nullptr, st, ctx.err);
-    if (pk.n_items > kNoallocMaxItems) {
-        snprintf(msg, sizeof msg, "lk_verify_noalloc: %lld work items exceed the static limit of %lld",
-                 (long long)pk.n_items, (long long)kNoallocMaxItems);
+    if (pk.n_items > kNoallocMaxItems || pk.n_chunk_bits > kNoallocMaxChunkBits) {
+        snprintf(msg, sizeof msg,
+                 "lk_verify_noalloc: %lld work items (%lld chunk slots of large pairs) exceed the static limit of "
+                 "%lld (%lld)", (long long)pk.n_items, (long long)pk.n_chunk_bits, (long long)kNoallocMaxItems,
+                 (long long)kNoallocMaxChunkBits);
         return fail(nullptr, LK_ERR_ARG, msg);
     }
     // Geometry into the scratch: offsets, then the vertices as resident FP64
@@ -1306,7 +1420,7 @@ extern "C" lk_status lk_verify_noalloc(const void* vertices, lk_dtype vdtype, in
                                   ctx.d_box_keys + 6 * n_loops, ctx.d_aabb, ctx.d_R, vsrc, vdtype == LK_F32 ? 0 : 1, 0,
                                   s);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "lk_verify_noalloc: geometry");
-    if ((st = ensure_workspace(&ctx, ws, n_pairs, pk.n_items, pk.n_chunks)) != LK_OK ||
+    if ((st = ensure_workspace(&ctx, ws, n_pairs, pk.n_items, pk.n_chunks, &pk)) != LK_OK ||
         (st = upload_packed(&ctx, ws, pk, s)) != LK_OK || (st = enqueue_verify(&ctx, ws, pk, s)) != LK_OK ||
         (st = copy_outputs(&ctx, ws, n_pairs, lk_out, raw_out, status_out, s)) != LK_OK)
         return fail(nullptr, st, ctx.err);
@@ -2015,53 +2129,87 @@ extern "C" lk_status lk_verify_expected(lk_ctx* ctx, const int32_t* loop_pairs, 
     *n_checked = 0;
     if (n_pairs == 0) return LK_OK;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    std::vector<int32_t> hp, he((size_t)n_pairs);
+    std::vector<int32_t> hp;
     lk_status st = get_pairs_on_host(ctx, loop_pairs, n_pairs, s, hp);
     if (st != LK_OK) return st;
-    if (is_device_ptr(expected)) {
-        LK_CUDA(ctx, cudaMemcpyAsync(he.data(), expected, n_pairs * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        LK_CUDA(ctx, cudaStreamSynchronize(s));
-    } else {
-        std::memcpy(he.data(), expected, n_pairs * sizeof(int32_t));
-    }
-    const int64_t budget = batch_segment_pairs > 0 ? batch_segment_pairs : ((int64_t)1 << 30);
-    std::vector<int32_t> blk, bst;
-    int64_t b0 = 0;
-    while (b0 < n_pairs) {
-        // next batch: at least one pair, up to the segment-pair budget
-        int64_t b1 = b0, sp = 0;
-        while (b1 < n_pairs) {
-            const int32_t a = hp[2 * b1], b = hp[2 * b1 + 1];
+    // Batches in input order: at least one pair each, up to the segment-pair budget.
+    const int64_t budget = batch_segment_pairs > 0 ? batch_segment_pairs : ((int64_t)1 << 28);
+    std::vector<int64_t> bounds{0};
+    {
+        int64_t sp = 0;
+        for (int64_t b = 0; b < n_pairs; ++b) {
+            const int32_t x = hp[2 * b], y = hp[2 * b + 1];
             int64_t c = 0;
-            if (a >= 0 && b >= 0 && a < ctx->n_loops && b < ctx->n_loops)
-                c = (ctx->h_offsets[a + 1] - ctx->h_offsets[a]) * (ctx->h_offsets[b + 1] - ctx->h_offsets[b]);
-            if (b1 > b0 && sp + c > budget) break;
-            sp += c;
-            ++b1;
-        }
-        const int64_t m = b1 - b0;
-        Packed pk;
-        if ((st = pack_pairs(ctx, hp.data() + 2 * b0, m, pk)) != LK_OK) return st;
-        if ((st = ensure_workspace(ctx, ctx->ws, m, pk.n_items, pk.n_chunks, &pk)) != LK_OK) return st;
-        if ((st = upload_packed(ctx, ctx->ws, pk, s)) != LK_OK) return st;
-        if ((st = enqueue_verify(ctx, ctx->ws, pk, s)) != LK_OK) return st;
-        note_stats(ctx, ctx->ws, pk, s);
-        if ((st = copy_outputs(ctx, ctx->ws, m, lk_out ? lk_out + b0 : nullptr, raw_out ? raw_out + b0 : nullptr,
-                               status_out ? status_out + b0 : nullptr, s)) != LK_OK)
-            return st;
-        blk.resize((size_t)m);
-        bst.resize((size_t)m);
-        LK_CUDA(ctx, cudaMemcpyAsync(blk.data(), ctx->ws.lk.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        LK_CUDA(ctx, cudaMemcpyAsync(bst.data(), ctx->ws.status.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        LK_CUDA(ctx, cudaStreamSynchronize(s));
-        *n_checked = b1;
-        for (int64_t k = 0; k < m; ++k) {
-            if (bst[(size_t)k] != LK_OK || blk[(size_t)k] != he[(size_t)(b0 + k)]) {
-                *first_mismatch = b0 + k;
-                return LK_OK;
+            if (x >= 0 && y >= 0 && x < ctx->n_loops && y < ctx->n_loops)
+                c = (ctx->h_offsets[x + 1] - ctx->h_offsets[x]) * (ctx->h_offsets[y + 1] - ctx->h_offsets[y]);
+            if (b > bounds.back() && sp + c > budget) {
+                bounds.push_back(b);
+                sp = 0;
             }
+            sp += c;
         }
-        b0 = b1;
+        bounds.push_back(n_pairs);
     }
+    const size_t nb = bounds.size() - 1;
+    // Pack every batch first (their tables stay alive until the stream has
+    // copied them) and size the shared workspace for the largest.
+    std::vector<Packed> batches(nb);
+    Packed most;
+    int64_t max_tasks = 0, max_items = 0, max_chunks = 0;
+    for (size_t k = 0; k < nb; ++k) {
+        Packed& pk = batches[k];
+        if ((st = pack_pairs(ctx, hp.data() + 2 * bounds[k], bounds[k + 1] - bounds[k], pk)) != LK_OK) return st;
+        max_tasks = std::max<int64_t>(max_tasks, (int64_t)pk.tasks.size());
+        max_items = std::max(max_items, pk.n_items);
+        max_chunks = std::max(max_chunks, pk.n_chunks);
+        most.n_chunk_bits = std::max(most.n_chunk_bits, pk.n_chunk_bits);
+        if (!pk.grid.empty()) {
+            if (most.grid.empty()) most.grid.push_back(pk.grid[0]);
+            most.grid_cells = std::max(most.grid_cells, pk.grid_cells);
+            most.grid_rows = std::max(most.grid_rows, pk.grid_rows);
+            most.grid_cols = std::max(most.grid_cols, pk.grid_cols);
+        }
+    }
+    if ((st = ensure_workspace(ctx, ctx->ws, max_tasks, max_items, max_chunks, &most)) != LK_OK) return st;
+    const size_t n = (size_t)n_pairs;
+    LK_CUDA(ctx, ctx->ee_expected.ensure(n));
+    LK_CUDA(ctx, ctx->ee_lk.ensure(n));
+    LK_CUDA(ctx, ctx->ee_raw.ensure(n));
+    LK_CUDA(ctx, ctx->ee_status.ensure(n));
+    LK_CUDA(ctx, ctx->ee_stop.ensure(1));
+    LK_CUDA(ctx, cudaMemcpyAsync(ctx->ee_expected.p, expected, n * sizeof(int32_t), cudaMemcpyDefault, s));
+    LK_CUDA(ctx, cudaMemsetAsync(ctx->ee_stop.p, 0x7f, sizeof(long long), s));     // no mismatch yet
+    // Every batch is enqueued back to back: its kernels read the stop word and
+    // do nothing once an earlier batch has lowered it, so no host round trip
+    // separates the batches.
+    Workspace& ws = ctx->ws;
+    for (size_t k = 0; k < nb; ++k) {
+        const Packed& pk = batches[k];
+        const int64_t b0 = bounds[k], m = bounds[k + 1] - bounds[k];
+        if ((st = upload_packed(ctx, ws, pk, s)) != LK_OK) return st;
+        if ((st = enqueue_verify(ctx, ws, pk, s, ctx->ee_stop.p, b0)) != LK_OK) return st;
+        lk::launch_compare_expected(ws.lk.p, ws.status.p, ctx->ee_expected.p, m, b0, ctx->ee_stop.p, s);
+        LK_CUDA(ctx, cudaMemcpyAsync(ctx->ee_lk.p + b0, ws.lk.p, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        LK_CUDA(ctx, cudaMemcpyAsync(ctx->ee_raw.p + b0, ws.raw.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        LK_CUDA(ctx, cudaMemcpyAsync(ctx->ee_status.p + b0, ws.status.p, m * sizeof(int32_t),
+                                     cudaMemcpyDeviceToDevice, s));
+    }
+    LK_CUDA(ctx, cudaGetLastError());
+    long long stop = 0;
+    LK_CUDA(ctx, cudaMemcpyAsync(&stop, ctx->ee_stop.p, sizeof stop, cudaMemcpyDeviceToHost, s));
+    LK_CUDA(ctx, cudaStreamSynchronize(s));
+    note_stats(ctx, ws, batches.back(), s);
+    ctx->last_err = nullptr;             // the estimates of the batches are not kept
+    int64_t checked = n_pairs;
+    if (stop >= 0 && stop < n_pairs) {
+        *first_mismatch = stop;
+        checked = *std::upper_bound(bounds.begin(), bounds.end(), (int64_t)stop);   // end of its batch
+    }
+    *n_checked = checked;
+    if (lk_out) LK_CUDA(ctx, cudaMemcpyAsync(lk_out, ctx->ee_lk.p, checked * sizeof(int32_t), cudaMemcpyDefault, s));
+    if (raw_out) LK_CUDA(ctx, cudaMemcpyAsync(raw_out, ctx->ee_raw.p, checked * sizeof(double), cudaMemcpyDefault, s));
+    if (status_out)
+        LK_CUDA(ctx, cudaMemcpyAsync(status_out, ctx->ee_status.p, checked * sizeof(int32_t), cudaMemcpyDefault, s));
+    LK_CUDA(ctx, cudaStreamSynchronize(s));
     return LK_OK;
 }

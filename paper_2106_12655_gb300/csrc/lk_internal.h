@@ -37,6 +37,18 @@ constexpr double kChunkFixScale = 4294967296.0;  // 2^32
 // Per-pair flag bits.
 constexpr int kFlagIntersect = 1;
 constexpr int kFlagCcFallback = 2;   // counting crossings could not decide the pair: direct sum
+constexpr int kFlagPrecise = 4;      // the pair's bulk chunks are summed again by the precise sweep
+
+// Error statistics of a work item's bulk sweep (SweepArgs::item_err), in units
+// of the FP32 unit roundoff u = 2^-24 where they scale with it:
+//   x: sum over its chunk columns of (a theta_c)^2 + 32 (b kq)^2 -- the variance
+//      of the item's rounding errors over u^2 (theta_c a column's angle over one
+//      32-row chunk, kq = L^2 / m^2 its lane's longest segment over nearest
+//      grid distance, squared; a, b below);
+//   y: sum of |theta_c| (radians);
+//   z: the largest kq;  w: unused.
+constexpr float kErrAcc = 4.0f;      // a: the running sum of a chunk column (measured: about 2)
+constexpr float kErrCell = 2.0f;     // b: one cell's terms relative to L^2 / m^2 (measured: at most 1)
 
 // One loop pair of a verify call, laid out for the device.
 //
@@ -70,7 +82,8 @@ struct PairTask {
     float row_off[4];    // frame offset of the row loop's vertices ([3] unused)
     float col_off[4];    // frame offset of the column loop's vertices ([3] unused)
     float scale;         // power of two
-    float pad2[3];
+    int32_t pad2;
+    int64_t bit_base;    // accurate variant: first bit of the pair's chunks in SweepArgs::chunk_bits
 };
 
 // A segment pair queued for FP64 recompute.
@@ -120,7 +133,24 @@ struct SweepArgs {
     int* cc_half;                  // [n_tasks] twice the linking number by crossings
     const unsigned int* flag_scan; // [n_tasks+1] exclusive scan of the item counts of pairs flagged
                                    // kFlagCcFallback; set: the direct-sum sweeps visit only those items
+    // Error statistics and the precise re-sweep (accurate-variant pairs).
+    float4* item_err;              // [n_items] bulk-sweep error statistics (see kErrAcc), or null
+    unsigned int* chunk_bits;      // bit per chunk of accurate-variant items (PairTask::bit_base):
+                                   // set when the bulk sweep handed the chunk to the careful pass
+                                   // (every chunk of an item handed over whole), or null
+    const unsigned int* precise_scan;  // [n_tasks+1] exclusive scan of the item counts of pairs flagged
+                                       // kFlagPrecise (read by the precise sweep)
+    // Early exit (lk_verify_expected): when *stop < stop_base, a pair before
+    // this batch already differs from its expected linking number and every
+    // kernel of the batch returns without work (the sweeps check before each
+    // item they take).  Null: no early exit.
+    const long long* stop;
+    long long stop_base;
 };
+
+__device__ __forceinline__ bool stopped(const long long* stop, long long base) {
+    return stop && *(volatile const long long*)stop < base;
+}
 
 // One request's contiguous run of items inside a serving wave.
 struct WaveSeg {
@@ -131,12 +161,17 @@ struct WaveSeg {
 
 struct ReduceArgs {
     const PairTask* tasks;
+    const float4* item_err;        // bulk-sweep error statistics, or null
+    double* err_out;               // [n_tasks] by out_index: estimated error of raw (see lk.h), or null
+    double precise_tol;            // flag accurate pairs whose estimate exceeds it kFlagPrecise (0: never)
+    const long long* stop;         // early exit, as in SweepArgs
+    long long stop_base;
     const int* cc_half;            // counting crossings: non-null selects it for unflagged pairs
     const int64_t* item_begin;
     const double* partial;
     const unsigned long long* item_fix;   // may be null
     const unsigned long long* fix_acc;
-    const int* flags;
+    int* flags;                    // kFlagPrecise is set here (precise_tol)
     int64_t n_tasks;
     double int_tol;
     int32_t* lk_out;               // indexed by out_index
@@ -200,10 +235,25 @@ size_t cc_local_smem_bytes(const CcLocalShape& S);
 // Counting crossings: scan[0..n_tasks] = exclusive scan of the item counts of
 // the pairs flagged kFlagCcFallback (block_sums: n_tasks / 4096 + 2 entries).
 void launch_cc_flag_scan(const SweepArgs& a, unsigned int* scan, unsigned int* block_sums, cudaStream_t s);
-void launch_cc_local(const SweepArgs& a, int64_t n_tasks, const CcLocalShape& S, cudaStream_t s);
+// scan[0..n_tasks] = exclusive scan of the item counts of the pairs whose flags have a bit of `mask`.
+void launch_flag_scan(const SweepArgs& a, int mask, unsigned int* scan, unsigned int* block_sums, cudaStream_t s);
+// The precise (compensated double-float) re-sweep of the bulk chunks of the
+// pairs flagged kFlagPrecise (a.precise_scan, a.chunk_bits set), and the
+// careful pass of their handed-over chunks (before launch_near_fix).
+void launch_sweep_precise(const SweepArgs& a, int64_t task_lo, int64_t task_hi, unsigned long long* counter,
+                          int grid, cudaStream_t s);
+void launch_precise_careful(const SweepArgs& a, unsigned long long* counter, int grid, cudaStream_t s);
+int sweep_precise_blocks_per_sm();
+// Early exit: *stop = min(*stop, base + k) for the first k in [0, n) whose
+// status is not LK_OK or whose linking number differs from expected[base + k]
+// (skipped when *stop < base already).
+void launch_compare_expected(const int32_t* lk, const int32_t* status, const int32_t* expected, int64_t n,
+                             long long base, long long* stop, cudaStream_t s);
+cudaError_t launch_cc_local(const SweepArgs& a, int64_t n_tasks, int64_t n_local, const CcLocalShape& S,
+                            cudaStream_t s);
 // G_max: the allocated grid size (offsets hold G_max^2 + 1 counts).
-void launch_cc_grid(const SweepArgs& a, int task, int n_rows, int n_cols, int G_max, const CcGridWork& w,
-                    cudaStream_t s);
+cudaError_t launch_cc_grid(const SweepArgs& a, int task, int n_rows, int n_cols, int G_max, const CcGridWork& w,
+                           cudaStream_t s);
 void launch_cc_resolve(const SweepArgs& a, int grid, cudaStream_t s);
 int cc_sweep_blocks_per_sm();
 

@@ -51,7 +51,7 @@ class lk_options(ctypes.Structure):
                 ("tile_rows", ctypes.c_int), ("near_capacity", ctypes.c_int),
                 ("timing", ctypes.c_int), ("chunk_capacity", ctypes.c_int),
                 ("accurate_threshold", ctypes.c_int64), ("method", ctypes.c_int),
-                ("cc_capacity", ctypes.c_int), ("cc_search", ctypes.c_int)]
+                ("cc_capacity", ctypes.c_int), ("cc_search", ctypes.c_int), ("precise_tol", ctypes.c_double)]
 
 
 class lk_stats(ctypes.Structure):
@@ -60,7 +60,8 @@ class lk_stats(ctypes.Structure):
                 ("near_overflow", ctypes.c_int64), ("tile_rows", ctypes.c_int32),
                 ("tile_cols", ctypes.c_int32), ("careful_items", ctypes.c_int64),
                 ("sweep_ms", ctypes.c_double), ("careful_chunks", ctypes.c_int64),
-                ("cc_candidates", ctypes.c_int64), ("cc_fallback_pairs", ctypes.c_int64)]
+                ("cc_candidates", ctypes.c_int64), ("cc_fallback_pairs", ctypes.c_int64),
+                ("precise_pairs", ctypes.c_int64)]
 
 
 class lk_server_options(ctypes.Structure):
@@ -114,6 +115,8 @@ def load(path: str | None = None):
     lib.lk_candidates.argtypes = [vp, vp, i64, ctypes.POINTER(i64), vp]
     lib.lk_get_stats.restype = ctypes.c_int
     lib.lk_get_stats.argtypes = [vp, ctypes.POINTER(lk_stats)]
+    lib.lk_get_error_estimates.restype = ctypes.c_int
+    lib.lk_get_error_estimates.argtypes = [vp, vp, i64, vp]
     lib.lk_get_options.restype = ctypes.c_int
     lib.lk_get_options.argtypes = [vp, ctypes.POINTER(lk_options)]
     lib.lk_destroy.restype = None
@@ -264,6 +267,12 @@ def lk_get_stats(ctx) -> dict:
     s = lk_stats()
     _check(load().lk_get_stats(ctx, ctypes.byref(s)), ctx)
     return {k: getattr(s, k) for k, _ in lk_stats._fields_}
+
+
+def lk_get_error_estimates(ctx, err_out, stream=None):
+    """err_out float64 [P] (host or device): the last verify's per-pair error estimates."""
+    n = int(err_out.shape[0]) if len(err_out.shape) > 0 else 0
+    _check(load().lk_get_error_estimates(ctx, _ptr(err_out), n, _stream(stream)), ctx)
 
 
 def lk_get_options(ctx) -> lk_options:

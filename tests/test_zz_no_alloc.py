@@ -87,3 +87,53 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
         noalloc(g, g.pairs[:10], on_device=False)
     assert ei.value.status == lk.LK_ERR_ARG
     assert "limit" in str(ei.value)
+
+
+def stacked_rings(n_rings=1024, nseg=256, dr=0.01, dz=0.003):
+    """Coaxial rings of radii 1 + k dr at heights k dz: no two link (lk = 0),
+    and each ring lies within a few segment lengths of its ten nearest
+    neighbours along its whole length, so most of each neighbour pair's
+    32-row chunks are near enough for the careful pass."""
+    loops = [W.circle([0.0, 0.0, k * dz], [1, 0, 0], [0, 1, 0], nseg, radius=1.0 + k * dr) for k in range(n_rings)]
+    pairs = [(a, b) for a in range(n_rings) for b in range(a + 1, min(n_rings, a + 12))]
+    return W.from_loops(loops, dtype=np.float32, pairs=pairs)
+
+
+def test_noalloc_allocates_nothing_past_the_chunk_list():
+    """A (2,3) torus link of 2 x 65,536 segments: 131,072 work items and about
+    10^6 32-row chunks, far more than the 65,536 entries of the static chunk
+    list.  The call must size its lists to the static array (before this was
+    fixed it asked for a larger list and reallocated it), match the closed
+    form -6 and lk_verify, and leave the device's free memory unchanged."""
+    g = W.torus_link(2, 3, 65_536, dtype=np.float32)
+    ref = regular(g, g.pairs)
+    first = noalloc(g, g.pairs, on_device=False)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    second = noalloc(g, g.pairs, on_device=False)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    for out in (first, second):
+        check_same(out, ref)
+        assert out[2][0] == lk.LK_OK and out[0][0] == -6
+        assert abs(out[1][0] + 6.0) <= RAW_TOL
+
+
+def test_noalloc_chunk_list_overflow_hands_whole_items_over():
+    """Near chunks beyond the static chunk list: the call hands whole work
+    items to the careful pass instead.  Every pair of coaxial rings has lk = 0;
+    the raw sums match lk_verify (whose list is large enough) and a seeded
+    sample of them the FP64 oracle."""
+    from oracle import oracle as O
+
+    g = stacked_rings()
+    assert g.pairs.shape[0] <= 16_384 and g.vertices.shape[0] <= 262_144
+    ref = regular(g, g.pairs)
+    out = noalloc(g, g.pairs, on_device=False)
+    check_same(out, ref)
+    assert np.all(out[2] == lk.LK_OK) and np.all(out[0] == 0)
+    assert np.max(np.abs(out[1])) <= RAW_TOL
+    pick = np.random.default_rng(4).choice(g.pairs.shape[0], 64, replace=False)
+    want = O.link_pairs(g.vertices, g.offsets, g.pairs[pick])
+    assert np.max(np.abs(out[1][pick] - want)) <= RAW_TOL
