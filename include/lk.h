@@ -124,10 +124,8 @@ typedef struct lk_options {
                             lk_get_error_estimates) exceeds precise_tol has its bulk sum formed
                             again with compensated FP32 arithmetic (every quantity an unevaluated
                             sum of two floats, errors near 1e-10 where FP32 terms reach 1e-5; about
-                            6 times the accurate variant's work), in the same call.  0 = never;
-                            default 1e-7, a tenth of the 1e-6 raw tolerance.  Such pairs' vertices
-                            (those of every accurate-variant pair) are staged on a 2^-22 grid of
-                            the pair's frame so that vertex differences are exact. */
+                            7 times the accurate variant's work), in the same call.  0 = never;
+                            default 5e-7, half of the 1e-6 raw tolerance. */
 } lk_options;
 
 typedef struct lk_stats {
@@ -240,13 +238,15 @@ lk_status lk_get_stats(lk_ctx* ctx, lk_stats* out);
  * where "exact" is the direct sum of the same staged polylines in exact
  * arithmetic (the integer linking number).  It is 4 standard deviations of
  * the bulk sweep's rounding errors (each work item records the sum of its
- * chunk columns' squared angles and a per-cell scale L^2/m^2: longest
- * segment over nearest grid distance), plus the part that a rounded |s|^2
- * shared by a whole row or column adds coherently, plus, for pairs of the
- * fast variant, 1e-8 times the summed |angle| for the bias of the hardware
- * approximations.  Segment pairs summed by the careful pass or in FP64 are
- * not included; pairs decided by counting crossings have 0; a pair whose
- * status is not LK_OK has NaN.  The estimate is not a bound.
+ * chunk columns' squared angles, a per-cell scale L^2/m^2 -- longest segment
+ * over nearest grid distance -- and a share for each chunk it hands to the
+ * careful pass), plus the part that a rounded |s|^2 shared by a whole row or
+ * column adds coherently, plus a relative bias times the summed |angle|
+ * (1e-8 for the fast variant's hardware approximations, 2e-10 for the
+ * accurate variant); for a pair summed again by the compensated sweep, the
+ * bulk estimate over 2^9.  Segment pairs recomputed in FP64 are not
+ * included; pairs decided by counting crossings have 0; a pair whose status
+ * is not LK_OK has NaN.  The estimate is not a bound.
  *  err_out : [n_pairs] double, host or device, in the order of the verify's
  *            pair list; n_pairs must equal that list's length.
  * Ordered on cuda_stream after the verify; returns after the copy when

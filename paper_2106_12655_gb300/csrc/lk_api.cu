@@ -205,6 +205,8 @@ struct lk_ctx {
     int64_t* d_pls_offsets = nullptr;    // [n_loops]
     int32_t* d_pls_pairs = nullptr;      // staging for host destinations
     int64_t pls_pairs_cap = 0;
+    unsigned long long* d_pls_order = nullptr;   // [pls_sort_size(n_loops)] sorted (x key, loop)
+    DevBuf<unsigned long long> pls_pair_keys;    // the pairs as (i << 32 | j), padded for the sort
     // List growth: after each lk_verify its work counters are copied to pinned
     // host memory on the stream; a later lk_verify reads them once the copy has
     // landed (without waiting for it) and enlarges any list that overflowed.
@@ -833,7 +835,7 @@ void lk_default_options(lk_options* opt) {
     opt->method = LK_METHOD_DS;
     opt->cc_capacity = 1 << 18;
     opt->cc_search = LK_CC_SEARCH_AUTO;
-    opt->precise_tol = 1e-7;
+    opt->precise_tol = 5e-7;
 }
 
 const char* lk_last_error(const lk_ctx* ctx) {
@@ -1038,18 +1040,23 @@ lk_status lk_candidates(lk_ctx* ctx, int32_t* pairs_out, int64_t capacity, int64
     *n_pairs = 0;
     const int64_t L = ctx->n_loops;
     if (L < 2) return LK_OK;
+    if (L > (int64_t)1 << 30) return fail(ctx, LK_ERR_ARG, "lk_candidates: too many loops");
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    const unsigned nsort = lk::pls_sort_size(L);
     if (!ctx->d_pls_keys) {
         cudaError_t e = cudaMalloc(&ctx->d_pls_keys, (size_t)L * 6 * sizeof(long long));
         if (e == cudaSuccess) e = cudaMalloc(&ctx->d_pls_counts, (size_t)L * sizeof(int32_t));
         if (e == cudaSuccess) e = cudaMalloc(&ctx->d_pls_offsets, (size_t)L * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_pls_order, (size_t)nsort * sizeof(unsigned long long));
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, LK_ERR_OOM, "lk_candidates: device allocation failed");
         }
     }
+    // sort by lower x, then count each loop's forward overlaps
     lk::launch_pls_keys(ctx->d_aabb, L, ctx->d_pls_keys, s);
-    lk::launch_pls_count(ctx->d_pls_keys, L, ctx->d_pls_counts, s);
+    lk::launch_pls_sort(ctx->d_pls_keys, L, ctx->d_pls_order, nsort, s);
+    lk::launch_pls_sweep_count(ctx->d_pls_keys, L, ctx->d_pls_order, ctx->d_pls_counts, s);
     std::vector<int32_t> counts((size_t)L);
     LK_CUDA(ctx, cudaMemcpyAsync(counts.data(), ctx->d_pls_counts, (size_t)L * sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, s));
@@ -1060,8 +1067,18 @@ lk_status lk_candidates(lk_ctx* ctx, int32_t* pairs_out, int64_t capacity, int64
         offsets[(size_t)i] = total;
         total += counts[(size_t)i];
     }
+    if (total > (int64_t)1 << 31) return fail(ctx, LK_ERR_ARG, "lk_candidates: more than 2^31 candidate pairs");
     const int64_t m = std::min(total, capacity);
     if (m > 0) {
+        // every pair as an (i << 32 | j) key, sorted into (i, j) order
+        const unsigned npk = lk::pls_sort_size(total);
+        LK_CUDA(ctx, ctx->pls_pair_keys.ensure(npk));
+        LK_CUDA(ctx, cudaMemsetAsync(ctx->pls_pair_keys.p, 0xff, (size_t)npk * sizeof(unsigned long long), s));
+        LK_CUDA(ctx, cudaMemcpyAsync(ctx->d_pls_offsets, offsets.data(), (size_t)L * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, s));
+        lk::launch_pls_sweep_write(ctx->d_pls_keys, L, ctx->d_pls_order, ctx->d_pls_offsets, ctx->pls_pair_keys.p,
+                                   total, s);
+        lk::launch_bitonic_sort(ctx->pls_pair_keys.p, npk, s);
         int32_t* dst = pairs_out;
         const bool host = !is_device_ptr(pairs_out);
         if (host) {
@@ -1077,9 +1094,7 @@ lk_status lk_candidates(lk_ctx* ctx, int32_t* pairs_out, int64_t capacity, int64
             }
             dst = ctx->d_pls_pairs;
         }
-        LK_CUDA(ctx, cudaMemcpyAsync(ctx->d_pls_offsets, offsets.data(), (size_t)L * sizeof(int64_t),
-                                     cudaMemcpyHostToDevice, s));
-        lk::launch_pls_write(ctx->d_pls_keys, L, ctx->d_pls_offsets, dst, m, s);
+        lk::launch_pls_unpack(ctx->pls_pair_keys.p, m, dst, s);
         LK_CUDA(ctx, cudaGetLastError());
         if (host)
             LK_CUDA(ctx, cudaMemcpyAsync(pairs_out, dst, (size_t)m * 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -1166,6 +1181,8 @@ void lk_destroy(lk_ctx* ctx) {
     if (ctx->d_pls_counts) cudaFree(ctx->d_pls_counts);
     if (ctx->d_pls_offsets) cudaFree(ctx->d_pls_offsets);
     if (ctx->d_pls_pairs) cudaFree(ctx->d_pls_pairs);
+    if (ctx->d_pls_order) cudaFree(ctx->d_pls_order);
+    ctx->pls_pair_keys.release();
     if (ctx->d_stage) cudaFree(ctx->d_stage);
     if (ctx->counters_ev) {
         cudaEventSynchronize(ctx->counters_ev);

@@ -47,8 +47,8 @@ constexpr int kFlagPrecise = 4;      // the pair's bulk chunks are summed again 
 //      grid distance, squared; a, b below);
 //   y: sum of |theta_c| (radians);
 //   z: the largest kq;  w: unused.
-constexpr float kErrAcc = 4.0f;      // a: the running sum of a chunk column (measured: about 2)
-constexpr float kErrCell = 2.0f;     // b: one cell's terms relative to L^2 / m^2 (measured: at most 1)
+constexpr float kErrAcc = 3.0f;      // a: the running sum of a chunk column (FP32 emulation: about 2)
+constexpr float kErrCell = 0.5f;     // b: a cell's rounding relative to L^2 / m^2 (analysis: about 1/4)
 
 // One loop pair of a verify call, laid out for the device.
 //
@@ -259,6 +259,16 @@ int cc_sweep_blocks_per_sm();
 
 // Potential link search (lk_pls.cu).
 void launch_pls_keys(const double* aabb, int64_t n_loops, long long* keys, cudaStream_t s);
+// Sort and sweep: pls_sort_size(n) is the padded length (a power of two) of
+// the 64-bit key arrays the bitonic sort takes.
+unsigned pls_sort_size(int64_t n);
+void launch_bitonic_sort(unsigned long long* a, unsigned n, cudaStream_t s);
+void launch_pls_sort(const long long* keys, int64_t n_loops, unsigned long long* order, unsigned n, cudaStream_t s);
+void launch_pls_sweep_count(const long long* keys, int64_t n_loops, const unsigned long long* order,
+                            int32_t* counts, cudaStream_t s);
+void launch_pls_sweep_write(const long long* keys, int64_t n_loops, const unsigned long long* order,
+                            const int64_t* offsets, unsigned long long* pairs, int64_t capacity, cudaStream_t s);
+void launch_pls_unpack(const unsigned long long* keys, int64_t n, int32_t* pairs, cudaStream_t s);
 void launch_pls_count(const long long* keys, int64_t n_loops, int32_t* counts, cudaStream_t s);
 void launch_pls_write(const long long* keys, int64_t n_loops, const int64_t* offsets, int32_t* pairs,
                       int64_t capacity, cudaStream_t s);
