@@ -218,9 +218,15 @@ lk_status lk_verify(lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs, int
  *              min(n, capacity) pairs (may be NULL when capacity = 0).
  *  n_pairs   : receives n, the number of candidate pairs (call with
  *              capacity 0 to size the output).
- * Synchronous: returns after the pairs are written.  Device memory: 60 bytes
- * per loop, plus 8 bytes per pair written to a host destination.  The test is
- * exact (FP64 box bounds) and costs L(L-1)/2 box tests for L loops.
+ * Synchronous: returns after the pairs are written.  The test is exact (FP64
+ * box bounds).  Up to 2^27 box pairs (L(L-1)/2 for L loops, about 16,000
+ * loops) every pair is tested; above, the loops are sorted by their lower x
+ * bound and each is tested only against those whose lower x bound falls in
+ * its x extent (a sort and sweep: work proportional to the pairs that overlap
+ * in x).  Device memory: 68 bytes per loop (plus 8 bytes per loop rounded up
+ * to a power of two for the sort), 8 bytes per candidate pair (rounded up
+ * likewise) in the sweep, plus 8 bytes per pair written to a host
+ * destination.
  * Errors: LK_ERR_ARG, LK_ERR_OOM, LK_ERR_CUDA.
  */
 lk_status lk_candidates(lk_ctx* ctx, int32_t* pairs_out, int64_t capacity, int64_t* n_pairs,

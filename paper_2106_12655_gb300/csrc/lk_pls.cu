@@ -9,7 +9,12 @@
 // double x with bits b (after mapping -0 to +0), key = b for x >= 0 and
 // key = b ^ 0x7fff...f for x < 0, so key(x) <= key(y) exactly when x <= y.
 //
-// Sort and sweep on one axis (Algorithm 2 builds a bounding-volume
+// Up to 2^27 box pairs the search tests every pair (tiled through shared
+// memory: one warp per row i, eight rows per block sharing each staged tile
+// of 256 boxes; a count pass, then a write pass at each row's offset, so the
+// list is in (i, j) order), which is faster than the sorts' launches there.
+//
+// Above that, sort and sweep on one axis (Algorithm 2 builds a bounding-volume
 // hierarchy; a sorted sweep finds the same set, with work proportional to the
 // pairs that overlap in x rather than to L^2): the loops are sorted by the
 // upper 32 bits of their lower x key (ties by loop index), and each loop

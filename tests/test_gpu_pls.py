@@ -131,3 +131,36 @@ def test_candidates_feed_verify_and_contain_every_linked_pair():
     ref = O.link_pairs(g.vertices, g.offsets, c)
     assert np.array_equal(lo.cpu().numpy(), O.round_lk(ref).astype(np.int32))
     assert np.abs(raw.cpu().numpy() - ref).max() <= 1e-6
+
+
+def test_sort_and_sweep_on_100k_loops():
+    """100,000 small triangles scattered so that each box overlaps about ten
+    others: the sort and sweep on x finds exactly the oracle's all-pairs set
+    (5e9 box tests on the host)."""
+    import time
+
+    g = grid_triangles(100_000, 5, spread=104)
+    ctx, stream = context(g)
+    try:
+        lk.lk_candidates(ctx, stream=stream)                  # first call allocates
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        got = lk.lk_candidates(ctx, stream=stream)
+        dt = time.perf_counter() - t0
+    finally:
+        lk.lk_destroy(ctx)
+    ref = O.candidates(g.vertices, g.offsets)
+    print(f"100k loops: {got.shape[0]} candidate pairs in {1e3 * dt:.2f} ms")
+    assert got.shape == ref.shape and np.array_equal(got, ref)
+    assert 100_000 < ref.shape[0] < 10_000_000
+
+
+def test_sort_and_sweep_with_exact_ties():
+    """20,000 triangles whose boxes sit on a coarse grid (many equal bounds,
+    boxes touching on faces, edges and corners): past 2^27 box pairs the
+    search sorts and sweeps, and must still equal the oracle exactly."""
+    g = grid_triangles(20_000, 3, spread=40)
+    assert 20_000 * 19_999 // 2 > (1 << 27)
+    got = gpu_candidates(g)
+    ref = O.candidates(g.vertices, g.offsets)
+    assert got.shape == ref.shape and np.array_equal(got, ref)
