@@ -51,7 +51,7 @@ KERNELS_PER_STEP = 6
 # DRAM bytes (read + write) of one sweep_packed_kernel<fast> launch on this
 # workload, from one ncu capture of the current kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); set to None whenever the kernel changes.
-SWEEP_TRAFFIC_BYTES = 10002688
+SWEEP_TRAFFIC_BYTES = 10007296
 
 
 def parse():
@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--precise-only", action="store_true",
+                    help="verify one woundball pair (nu = 10^3, 2 x 10^5 segments) twice, which the precise "
+                         "variant sums: for profiling that kernel")
     ap.add_argument("--headline-only", action="store_true",
                     help="time the headline step only (no tuning, FP64 baseline, end-to-end or other blocks): "
                          "for launch lists under a profiler")
@@ -173,14 +176,16 @@ def serving_block(args):
     try:
         warm = S.request_plan(scenes, 40, seed=99)
         S.run(srv, scenes, warm, None)
+        # capacity: a closed loop of at most 32 requests queued or running, so
+        # that the host packing of later requests overlaps the device work
         cap_plan = S.request_plan(scenes, max(100, args.serving_requests // 2), seed=1)
-        lat, wall, bad = S.run(srv, scenes, cap_plan, None)
+        lat, wall, bad = S.run(srv, scenes, cap_plan, None, max_outstanding=32)
         pairs, sps = S.plan_sizes(scenes, cap_plan)
         cap = len(cap_plan) / wall
         out = {"scenes": [{"rings": sc.geometry.n_loops, "vertices": int(sc.geometry.vertices.shape[0]),
                            "pairs": int(sc.geometry.pairs.shape[0])} for sc in scenes],
                "capacity": {"req_per_s": cap, "pairs_per_s": pairs.sum() / wall, "sp_per_s": sps.sum() / wall,
-                            "n_requests": len(cap_plan), "nonok_pair_status": bad},
+                            "n_requests": len(cap_plan), "nonok_pair_status": bad, "outstanding": 32},
                "loads": []}
         for load in (0.5, 0.8, 0.95):
             plan = S.request_plan(scenes, args.serving_requests, seed=int(load * 100))
@@ -308,6 +313,43 @@ def per_pair_block(g, v, off, lk_ref, stream, n_sample=512, seed=9):
             "value": float(sps) / (ms / 1e3), "unit": UNIT,
             "lk_equal_batched": bool(np.array_equal(lo_h, lk_ref[pick])),
             "all_status_ok": bool(np.all(st.cpu().numpy() == 0))}
+
+
+def early_exit_block(g, v, off, lk_ref, stream, batch=1 << 26, reps=5):
+    """Sec. 3.1's fast verification on the sheet (lk_verify_expected, batches
+    of 2^26 segment pairs, all enqueued at once; the first batch with a changed
+    linking number stops the later ones on the device): CUDA-event time of a
+    full check against the sheet's own certificate, and of a check whose
+    certificate differs at pair 100 (a "pull-through" among the first items),
+    each the median of `reps` after one untimed call."""
+    import torch
+    from paper_2106_12655_gb300 import lk
+
+    cert = np.ascontiguousarray(lk_ref.astype(np.int32))
+    bad = cert.copy()
+    bad[100] += 1
+    pairs_d = torch.from_numpy(np.ascontiguousarray(g.pairs)).cuda()
+    ctx = lk.lk_create(v, off, None, stream)
+    out = {}
+    try:
+        for label, c in (("full", cert), ("changed_at_100", bad)):
+            cd = torch.from_numpy(c).cuda()
+            ms, res = [], None
+            for k in range(reps + 1):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res = lk.lk_verify_expected(ctx, pairs_d, cd, batch, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                if k:
+                    ms.append(e0.elapsed_time(e1))
+            out[label] = {"ms": statistics.median(ms), "first_mismatch": int(res[0]), "pairs_checked": int(res[1])}
+    finally:
+        lk.lk_destroy(ctx)
+    out["batch_segment_pairs"] = batch
+    out["pairs"] = int(g.pairs.shape[0])
+    return out
 
 
 def timed_verify(ctx, pd, n, stream, warm, reps, device):
@@ -803,6 +845,7 @@ def run_ours(args):
     }
     if world == 1:
         line["one_call_per_pair"] = per_pair_block(g, v, off, lk_host, stream)
+        line["early_exit"] = early_exit_block(g, v, off, lk_host, stream)
         line["counting_crossings"] = counting_crossings_block(g, v, off, pairs_d, lk_host, stream, flush)
         line["counting_crossings_all_pairs_sweep"] = counting_crossings_block(
             g, v, off, pairs_d, lk_host, stream, flush, search=lk.LK_CC_SEARCH_SWEEP)
@@ -838,6 +881,9 @@ def summary(line):
     the closed form."""
     out = {"fp64_gpu": {"sp_s": _g(line["fp64_baseline"]["value"]),
                         "mixed_speedup": _g(line["fp64_baseline"]["speedup_mixed_over_fp64"])},
+           "early_exit_ms": ({"full": _g(line["early_exit"]["full"]["ms"]),
+                              "changed_at_100": _g(line["early_exit"]["changed_at_100"]["ms"])}
+                             if "early_exit" in line else None),
            "roofline_frac": _g(line["roofline"]["frac"]), "e2e_sp_s": _g(line["e2e"]["value"])}
     err, rate = {}, {}
     if "parity_vs_oracle" in line:
@@ -872,8 +918,38 @@ def summary(line):
     return out
 
 
+def run_precise_only(args):
+    """One pair that the bulk sweep's error estimate sends to the precise
+    variant, verified twice (CUDA-event time of the second)."""
+    import torch
+    from paper_2106_12655_gb300 import build as B
+    from paper_2106_12655_gb300 import lk
+    from paper_2106_12655_gb300 import workloads as W
+
+    B.build()
+    lk.load()
+    g = W.woundball(1000, 100_000)
+    g.vertices = g.vertices.astype(np.float32)
+    stream = torch.cuda.current_stream()
+    v = torch.from_numpy(g.vertices).cuda()
+    off = torch.from_numpy(g.offsets).cuda()
+    ctx = lk.lk_create(v, off, None, stream)
+    try:
+        pd = torch.from_numpy(g.pairs).cuda()
+        ms, lo, raw, st, est = timed_verify(ctx, pd, 1, stream, 1, 1, v.device)
+        stats = lk.lk_get_stats(ctx)
+    finally:
+        lk.lk_destroy(ctx)
+    print(json.dumps({"workload": "woundball nu=1000, 2 x 100,000 segments", "segment_pairs": g.segment_pairs(),
+                      "ms": ms[0], "raw": float(raw[0]), "lk": int(lo[0]), "status": int(st[0]),
+                      "error_estimate": float(est[0]), "precise_pairs": stats["precise_pairs"]}), flush=True)
+
+
 def main():
     args = parse()
+    if args.precise_only:
+        run_precise_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

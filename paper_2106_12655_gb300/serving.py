@@ -58,10 +58,14 @@ def request_plan(scenes, n_requests, seed=0, min_pairs=1000, max_pairs=20000):
     return plan
 
 
-def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0):
+def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0, max_outstanding=None):
     """Serve `plan`; arrivals are Poisson at rate_per_s (None: all at t = 0).
-    Returns per-request latencies (s), the wall time, and the number of pair
-    results whose status was not LK_OK."""
+    With max_outstanding, a request is submitted only while fewer than that
+    many are queued or running (a closed loop: with rate_per_s None this
+    measures the sustained capacity, the host packing of later requests
+    overlapping the device work of earlier ones).  Returns per-request
+    latencies (s), the wall time, and the number of pair results whose status
+    was not LK_OK."""
     rng = np.random.default_rng(seed)
     n = len(plan)
     if rate_per_s is None:
@@ -80,7 +84,7 @@ def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0
         now = time.perf_counter() - t0
         if now > timeout_s:
             raise TimeoutError("serving run exceeded %.0f s" % timeout_s)
-        while nxt < n and arrivals[nxt] <= now:
+        while nxt < n and arrivals[nxt] <= now and (max_outstanding is None or len(pending) < max_outstanding):
             k, pairs = plan[nxt]
             sc = scenes[k]
             if update and sc.in_flight == 0:
@@ -100,7 +104,7 @@ def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0
                 lat[i] = (time.perf_counter() - t0) - arrivals[i]
                 scenes[k].in_flight -= 1
                 done += 1
-        if not pending and nxt < n:
+        if not pending and nxt < n and arrivals[nxt] > time.perf_counter() - t0:
             wait = arrivals[nxt] - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(min(wait, 0.001))
