@@ -302,7 +302,11 @@ void lk_plan_destroy(lk_plan* plan);
  * the later batches reads that word first -- the persistent sweeps before
  * each work item they take -- and does nothing once it is set, so the work
  * after the first differing batch costs only its launches.  No kernel waits
- * on the word.
+ * on the word.  A call with the same pair list and batch size as the previous
+ * call on this context builds (once, up to 256 batches) a CUDA graph of the
+ * whole batched sequence with the batches' item tables resident, and later
+ * such calls upload the certificate and replay it: no host packing, one
+ * launch.  A different list or batch size drops that graph.
  *  *first_mismatch : the smallest mismatching index of the first batch that
  *                    has one, or -1 if every pair matches.
  *  *n_checked      : pairs verified before stopping (a prefix of the list:
