@@ -315,9 +315,9 @@ def per_pair_block(g, v, off, lk_ref, stream, n_sample=512, seed=9):
             "all_status_ok": bool(np.all(st.cpu().numpy() == 0))}
 
 
-def early_exit_block(g, v, off, lk_ref, stream, batch=1 << 26, reps=5):
+def early_exit_block(g, v, off, lk_ref, stream, batch=1 << 27, reps=5):
     """Sec. 3.1's fast verification on the sheet (lk_verify_expected, batches
-    of 2^26 segment pairs, all enqueued at once; the first batch with a changed
+    of 2^27 segment pairs, all enqueued at once; the first batch with a changed
     linking number stops the later ones on the device): CUDA-event time of a
     full check against the sheet's own certificate, and of a check whose
     certificate differs at pair 100 (a "pull-through" among the first items),
