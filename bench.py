@@ -179,7 +179,7 @@ def serving_block(args):
         # capacity: a closed loop of at most 32 requests queued or running, so
         # that the host packing of later requests overlaps the device work
         cap_plan = S.request_plan(scenes, max(100, args.serving_requests // 2), seed=1)
-        lat, wall, bad = S.run(srv, scenes, cap_plan, None, max_outstanding=32)
+        lat, wall, bad, _ = S.run(srv, scenes, cap_plan, None, max_outstanding=32)
         pairs, sps = S.plan_sizes(scenes, cap_plan)
         cap = len(cap_plan) / wall
         out = {"scenes": [{"rings": sc.geometry.n_loops, "vertices": int(sc.geometry.vertices.shape[0]),
@@ -189,7 +189,7 @@ def serving_block(args):
                "loads": []}
         for load in (0.5, 0.8, 0.95):
             plan = S.request_plan(scenes, args.serving_requests, seed=int(load * 100))
-            lat, wall, bad = S.run(srv, scenes, plan, rate_per_s=load * cap, seed=int(load * 1000))
+            lat, wall, bad, _ = S.run(srv, scenes, plan, rate_per_s=load * cap, seed=int(load * 1000))
             pairs, sps = S.plan_sizes(scenes, plan)
             out["loads"].append({"load": load, "offered_req_per_s": load * cap, "req_per_s": len(plan) / wall,
                                  "pairs_per_s": pairs.sum() / wall, "sp_per_s": sps.sum() / wall,
@@ -198,6 +198,45 @@ def serving_block(args):
                                  "n_requests": len(plan), "nonok_pair_status": bad})
         out["server_stats"] = lk.lk_server_get_stats(srv)
         out["potential_link_search"] = pls_block(scenes)
+        return out
+    finally:
+        lk.lk_server_destroy(srv)
+        S.close(scenes)
+
+
+def geometry_serving_block(args):
+    """Requests that carry geometry only: each verifies every potential link of
+    one of six resident piles (170-3,500 rings, 64-256 segments per ring, so
+    about 1k-20k candidate pairs), after a small displacement of the pile.
+    Served two ways on the same piles: the device search and packing of
+    lk_server_submit_geometry, and a host round trip (lk_candidates on the
+    server's stream, then lk_server_submit of the list).  Closed-loop capacity
+    (32 outstanding), then p50/p99 at 50% and 80% of each way's capacity."""
+    from paper_2106_12655_gb300 import lk
+    from paper_2106_12655_gb300 import serving as S
+
+    scenes = S.make_scenes(seed=7, n_scenes=6, min_rings=170, max_rings=3500)
+    srv = lk.lk_server_create(None)
+    try:
+        out = {"scenes": [{"rings": sc.geometry.n_loops, "pairs": int(sc.geometry.pairs.shape[0])} for sc in scenes]}
+        for mode in ("geometry", "host_search"):
+            S.run(srv, scenes, S.geometry_plan(scenes, 40, seed=98), None, max_outstanding=32, mode=mode)
+            plan = S.geometry_plan(scenes, max(100, args.serving_requests // 2), seed=2)
+            lat, wall, bad, verified = S.run(srv, scenes, plan, None, max_outstanding=32, mode=mode)
+            cap = len(plan) / wall
+            res = {"capacity": {"req_per_s": cap, "pairs_per_s": verified / wall, "n_requests": len(plan),
+                                "nonok_pair_status": bad}, "loads": []}
+            for load in (0.5, 0.8):
+                plan = S.geometry_plan(scenes, args.serving_requests, seed=int(load * 100) + 1)
+                lat, wall, bad, verified = S.run(srv, scenes, plan, rate_per_s=load * cap, seed=int(load * 1000) + 1,
+                                                 mode=mode)
+                res["loads"].append({"load": load, "offered_req_per_s": load * cap, "req_per_s": len(plan) / wall,
+                                     "pairs_per_s": verified / wall,
+                                     "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                                     "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                                     "n_requests": len(plan), "nonok_pair_status": bad})
+            out[mode] = res
+        out["server_stats"] = lk.lk_server_get_stats(srv)
         return out
     finally:
         lk.lk_server_destroy(srv)
@@ -853,6 +892,7 @@ def run_ours(args):
             g, v, off, pairs_d, lk_host, stream, flush, search=lk.LK_CC_SEARCH_SWEEP)
     if not args.no_serving and world == 1:
         line["serving"] = serving_block(args)
+        line["serving_geometry"] = geometry_serving_block(args)
     if not args.no_stress and world == 1:
         line["stress"] = stress_block(stream)
         line["configs"] = configs_block(stream)
@@ -896,6 +936,12 @@ def summary(line):
                           "n_req": sv["loads"][0]["n_requests"],
                           "p50_ms": [_g(x["p50_ms"]) for x in sv["loads"]],
                           "p99_ms": [_g(x["p99_ms"]) for x in sv["loads"]]}
+    if "serving_geometry" in line:
+        sg = line["serving_geometry"]
+        out["serving_geometry"] = {m: {"cap_req_s": _g(sg[m]["capacity"]["req_per_s"]),
+                                       "p50_ms": [_g(x["p50_ms"]) for x in sg[m]["loads"]],
+                                       "p99_ms": [_g(x["p99_ms"]) for x in sg[m]["loads"]]}
+                                   for m in ("geometry", "host_search")}
     if "configs" in line:
         c = line["configs"]
         err["ring_chain"] = _g(c["ring_chain"]["raw_err_vs_oracle"]["max"])

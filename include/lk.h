@@ -386,6 +386,8 @@ typedef struct lk_server_stats {
                                             (evaluated in place, slowly): raise near_capacity */
     int64_t careful_items;               /* whole items swept again per pair (chunk list full) */
     int64_t careful_chunks;              /* 32-row chunks swept again per pair */
+    int64_t geometry_requests;           /* submitted by lk_server_submit_geometry */
+    int64_t candidate_pairs;             /* pairs their potential link searches found */
 } lk_server_stats;
 
 void lk_server_default_options(lk_server_options* opt);
@@ -398,14 +400,39 @@ void* lk_server_stream(lk_server* srv);
  * full); LK_ERR_OOM (the request alone exceeds the arena). */
 lk_status lk_server_submit(lk_server* srv, lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs,
                            int64_t* ticket);
+/* Queue a request that carries geometry only: verify every potential link of
+ * ctx, the loop pairs (i, j), i < j, whose bounding boxes overlap (Sec. 3.2,
+ * Algorithm 2; every other pair has linking number 0).  The search, the
+ * packing of its pairs into work items and the sweep all run on the device:
+ * no pair list passes through the host, which reads back only the number of
+ * candidates and of work items (polled by lk_server_step, never waited for).
+ * The search runs on an internal stream after the work enqueued on
+ * lk_server_stream before this call (an lk_update of ctx there, say).  The
+ * pairs are the ones lk_candidates returns, in the same (i, j) order, and each
+ * pair's result equals lk_verify's for that list.  Results:
+ * lk_server_poll_pairs.  Errors: LK_ERR_ARG (not a mixed-precision context;
+ * more than 2^30 loops); LK_ERR_BUSY (queue full); LK_ERR_OOM (the search
+ * alone exceeds the arena).  A request whose candidates or work items do not
+ * fit the arena fails when it is polled (LK_ERR_OOM). */
+lk_status lk_server_submit_geometry(lk_server* srv, lk_ctx* ctx, int64_t* ticket);
 /* Retire finished waves, admit, launch the next wave.  wait = 1 also blocks
  * until the oldest wave in flight has finished. */
 lk_status lk_server_step(lk_server* srv, int wait);
 /* *done = 1 and the results copied to the host buffers ([n_pairs] each, may
  * be NULL) once the request has finished; the ticket is then released.
- * *done = 0 while it is queued or running. */
+ * *done = 0 while it is queued or running.  Not for geometry requests
+ * (LK_ERR_ARG): their pair count is known only to lk_server_poll_pairs. */
 lk_status lk_server_poll(lk_server* srv, int64_t ticket, int* done, int32_t* lk_out, double* raw_out,
                          int32_t* status_out);
+/* Poll any request, with its pair list: once it has finished, *done = 1 and
+ * *n_pairs receives its number of pairs.  If capacity >= *n_pairs the pairs
+ * ([2 * n] int32: loop i, loop j) and their results ([n] each) are copied to
+ * the non-NULL buffers and the ticket is released; otherwise nothing is
+ * copied and the ticket stays valid for a call with a larger buffer.  A
+ * geometry request's pairs are in (i, j) order, i < j.  Returns the request's
+ * error (and releases the ticket) if it could not run. */
+lk_status lk_server_poll_pairs(lk_server* srv, int64_t ticket, int* done, int64_t* n_pairs, int32_t* pairs_out,
+                               int64_t capacity, int32_t* lk_out, double* raw_out, int32_t* status_out);
 /* Tickets of requests that have finished (as seen by lk_server_step) and were
  * not reported before, in completion order: up to capacity of them are
  * written to tickets[], *n_done receives how many.  A reported ticket stays

@@ -232,7 +232,9 @@ struct lk_ctx {
     // Potential link search buffers (allocated on first use).
     long long* d_pls_keys = nullptr;     // [6][n_loops]
     int32_t* d_pls_counts = nullptr;     // [n_loops]
-    int64_t* d_pls_offsets = nullptr;    // [n_loops]
+    int64_t* d_pls_offsets = nullptr;    // [n_loops + 1] exclusive scan of the counts (total last)
+    long long* d_pls_scan = nullptr;     // the scan's block totals
+    int64_t* h_pls_total = nullptr;      // pinned: the candidate count
     int32_t* d_pls_pairs = nullptr;      // staging for host destinations
     int64_t pls_pairs_cap = 0;
     unsigned long long* d_pls_order = nullptr;   // [pls_sort_size(n_loops)] sorted (x key, loop)
@@ -983,6 +985,7 @@ lk_status lk_create(lk_ctx** out, const void* vertices, lk_dtype vdtype, int64_t
     ctx->box_set = 1;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counters, 10 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pls_total, sizeof(int64_t));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->counters_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         const lk_status st = cuda_fail(nullptr, e, "lk_create");
@@ -1079,7 +1082,8 @@ lk_status lk_candidates(lk_ctx* ctx, int32_t* pairs_out, int64_t capacity, int64
     if (!ctx->d_pls_keys) {
         cudaError_t e = cudaMalloc(&ctx->d_pls_keys, (size_t)L * 6 * sizeof(long long));
         if (e == cudaSuccess) e = cudaMalloc(&ctx->d_pls_counts, (size_t)L * sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_pls_offsets, (size_t)L * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_pls_offsets, ((size_t)L + 1) * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_pls_scan, lk::scan_scratch_count(L) * sizeof(long long));
         if (e == cudaSuccess) e = cudaMalloc(&ctx->d_pls_order, (size_t)nsort * sizeof(unsigned long long));
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -1098,16 +1102,12 @@ lk_status lk_candidates(lk_ctx* ctx, int32_t* pairs_out, int64_t capacity, int64
     } else {
         lk::launch_pls_count(ctx->d_pls_keys, L, ctx->d_pls_counts, s);
     }
-    std::vector<int32_t> counts((size_t)L);
-    LK_CUDA(ctx, cudaMemcpyAsync(counts.data(), ctx->d_pls_counts, (size_t)L * sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, s));
-    LK_CUDA(ctx, cudaStreamSynchronize(s));
-    std::vector<int64_t> offsets((size_t)L);
+    // offsets = exclusive scan of the counts on the device; only the total comes back
+    lk::launch_scan_counts(ctx->d_pls_counts, L, ctx->d_pls_offsets, ctx->d_pls_scan, s);
     int64_t total = 0;
-    for (int64_t i = 0; i < L; ++i) {
-        offsets[(size_t)i] = total;
-        total += counts[(size_t)i];
-    }
+    LK_CUDA(ctx, cudaMemcpyAsync(ctx->h_pls_total, ctx->d_pls_offsets + L, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    LK_CUDA(ctx, cudaStreamSynchronize(s));
+    total = *ctx->h_pls_total;
     if (total > (int64_t)1 << 31) return fail(ctx, LK_ERR_ARG, "lk_candidates: more than 2^31 candidate pairs");
     const int64_t m = std::min(total, capacity);
     if (m > 0 && !sweep) {
@@ -1126,8 +1126,6 @@ lk_status lk_candidates(lk_ctx* ctx, int32_t* pairs_out, int64_t capacity, int64
             }
             dst = ctx->d_pls_pairs;
         }
-        LK_CUDA(ctx, cudaMemcpyAsync(ctx->d_pls_offsets, offsets.data(), (size_t)L * sizeof(int64_t),
-                                     cudaMemcpyHostToDevice, s));
         lk::launch_pls_write(ctx->d_pls_keys, L, ctx->d_pls_offsets, dst, m, s);
         LK_CUDA(ctx, cudaGetLastError());
         if (host)
@@ -1138,8 +1136,6 @@ lk_status lk_candidates(lk_ctx* ctx, int32_t* pairs_out, int64_t capacity, int64
         const unsigned npk = lk::pls_sort_size(total);
         LK_CUDA(ctx, ctx->pls_pair_keys.ensure(npk));
         LK_CUDA(ctx, cudaMemsetAsync(ctx->pls_pair_keys.p, 0xff, (size_t)npk * sizeof(unsigned long long), s));
-        LK_CUDA(ctx, cudaMemcpyAsync(ctx->d_pls_offsets, offsets.data(), (size_t)L * sizeof(int64_t),
-                                     cudaMemcpyHostToDevice, s));
         lk::launch_pls_sweep_write(ctx->d_pls_keys, L, ctx->d_pls_order, ctx->d_pls_offsets, ctx->pls_pair_keys.p,
                                    total, s);
         lk::launch_bitonic_sort(ctx->pls_pair_keys.p, npk, s);
@@ -1248,6 +1244,8 @@ void lk_destroy(lk_ctx* ctx) {
     if (ctx->d_pls_keys) cudaFree(ctx->d_pls_keys);
     if (ctx->d_pls_counts) cudaFree(ctx->d_pls_counts);
     if (ctx->d_pls_offsets) cudaFree(ctx->d_pls_offsets);
+    if (ctx->d_pls_scan) cudaFree(ctx->d_pls_scan);
+    if (ctx->h_pls_total) cudaFreeHost(ctx->h_pls_total);
     if (ctx->d_pls_pairs) cudaFree(ctx->d_pls_pairs);
     if (ctx->d_pls_order) cudaFree(ctx->d_pls_order);
     ctx->pls_pair_keys.release();
@@ -1572,7 +1570,7 @@ struct Arena {
     }
 };
 
-enum ReqState { kQueued = 0, kRunning = 1, kLaunched = 2, kDone = 3 };
+enum ReqState { kQueued = 0, kRunning = 1, kLaunched = 2, kDone = 3, kSearching = 4, kPacking = 5 };
 
 struct Request {
     int64_t ticket = 0;
@@ -1580,6 +1578,9 @@ struct Request {
     std::vector<int32_t> pairs;
     Packed pk;
     bool packed = false;
+    // The counts the waves and the finishing passes need (from pk, or for a
+    // geometry request from the device packer's totals).
+    int64_t n_tasks = 0, n_items = 0, n_acc_items = 0, n_chunks = 0;
     Workspace ws;              // pointers into the device arena
     size_t dev_off = 0, dev_bytes = 0;
     size_t host_off = 0, host_bytes = 0;
@@ -1590,6 +1591,24 @@ struct Request {
     lk::SweepArgs args{};
     int64_t next_item = 0;
     int state = kQueued;
+    // Geometry requests: the pairs are the potential link search's candidates
+    // of the context, found and packed on the device (lk_server_submit_geometry).
+    bool geometry = false;
+    bool sweep = false;                  // sort-and-sweep search (else every box pair)
+    bool tuned = false;                  // the context's tune table goes to the packer
+    lk_status error = LK_OK;             // set when the request could not run
+    std::string error_msg;
+    cudaEvent_t ev = nullptr;            // end of the search, then of the packing
+    size_t scr_off = 0, scr_bytes = 0;   // device: the search's scratch (until packed)
+    size_t blk_off = 0, blk_bytes = 0;   // device: the pair list, keys and tasks (until done)
+    size_t sum_off = 0, sum_bytes = 0;   // pinned: the totals read back, the tune table
+    long long* h_sum = nullptr;          // [0] candidate pairs, [1..4] lk::PackSums of the packing
+    int32_t* h_pairs = nullptr;          // pinned copy of the pair list (results)
+    int32_t* d_pairs = nullptr;
+    lk::PackSums* d_totals = nullptr;    // [n_tasks] entry of the packing's scan
+    ~Request() {
+        if (ev) cudaEventDestroy(ev);
+    }
 };
 
 struct Wave {
@@ -1603,10 +1622,12 @@ constexpr int kWaveSlots = 3;          // waves in flight at most
 constexpr int kMaxSegs = 256;          // request runs per wave
 
 // Carve one request's work buffers out of the arena at `base` (or, with
-// base = 0, only measure them); returns the bytes used.
-size_t request_layout(const Packed& pk, int near_cap, Workspace* ws, uintptr_t base) {
+// base = 0, only measure them); returns the bytes used.  Without `tables` the
+// pair tasks and item_begin live elsewhere (a geometry request's pack block).
+size_t request_layout(int64_t n_tasks, int64_t n_items, int64_t n_chunks, bool tables, int near_cap, Workspace* ws,
+                      uintptr_t base) {
     size_t off = 0;
-    const size_t P = std::max<size_t>(pk.tasks.size(), 1), I = (size_t)std::max<int64_t>(pk.n_items, 1);
+    const size_t P = (size_t)std::max<int64_t>(n_tasks, 1), I = (size_t)std::max<int64_t>(n_items, 1);
     auto bind = [&](auto& buf, size_t count) {
         using T = typename std::remove_pointer<decltype(buf.p)>::type;
         off = (off + 255) & ~(size_t)255;
@@ -1614,12 +1635,14 @@ size_t request_layout(const Packed& pk, int near_cap, Workspace* ws, uintptr_t b
         buf.cap = count;
         off += count * sizeof(T);
     };
-    bind(ws->tasks, P);
-    bind(ws->item_begin, P + 1);
+    if (tables) {
+        bind(ws->tasks, P);
+        bind(ws->item_begin, P + 1);
+    }
     bind(ws->item_task, I);
     bind(ws->partial, I);
     bind(ws->careful_items, I);
-    bind(ws->careful_chunks, (size_t)std::max<int64_t>(1, std::min<int64_t>(pk.n_chunks, (int64_t)1 << 16)));
+    bind(ws->careful_chunks, (size_t)std::max<int64_t>(1, std::min<int64_t>(n_chunks, (int64_t)1 << 16)));
     bind(ws->item_fix, I);
     bind(ws->near_list, (size_t)near_cap);
     bind(ws->fix_acc, P);
@@ -1632,10 +1655,81 @@ size_t request_layout(const Packed& pk, int near_cap, Workspace* ws, uintptr_t b
     return off;
 }
 
+size_t request_layout(const Packed& pk, int near_cap, Workspace* ws, uintptr_t base) {
+    return request_layout((int64_t)pk.tasks.size(), pk.n_items, pk.n_chunks, true, near_cap, ws, base);
+}
+
+// Sequential 256-byte aligned pieces of one arena block (base 0: measure only).
+struct Carver {
+    uintptr_t base;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// A geometry request's search scratch: box keys, per-loop counts and offsets,
+// the scan's block totals, the sweep's sorted order, the tune table.
+struct SearchBufs {
+    long long* keys;
+    int32_t* counts;
+    int64_t* offsets;
+    long long* scan;
+    unsigned long long* order;
+    int32_t* tune;
+};
+
+size_t search_layout(int64_t L, bool sweep, SearchBufs* b, uintptr_t base) {
+    Carver c{base};
+    b->keys = c.take<long long>((size_t)L * 6);
+    b->counts = c.take<int32_t>((size_t)L);
+    b->offsets = c.take<int64_t>((size_t)L + 1);
+    b->scan = c.take<long long>(lk::scan_scratch_count(L));
+    b->order = sweep ? c.take<unsigned long long>(lk::pls_sort_size(L)) : nullptr;
+    b->tune = c.take<int32_t>((size_t)lk::kTuneClasses * lk::kTuneClasses);
+    return c.off;
+}
+
+// Its pack block: the pair list, the 64-bit keys of both sorts, the tasks,
+// their counts and scan, item_begin.
+struct PackBufs {
+    int32_t* pairs;
+    unsigned long long* keys;
+    PairTask* tasks;
+    lk::PackSums* sums;
+    lk::PackSums* scan;
+    lk::PackSums* scratch;
+    int64_t* item_begin;
+};
+
+size_t pack_layout(int64_t T, PackBufs* b, uintptr_t base) {
+    Carver c{base};
+    b->pairs = c.take<int32_t>((size_t)T * 2);
+    b->keys = c.take<unsigned long long>(lk::pls_sort_size(T));
+    b->tasks = c.take<PairTask>((size_t)T);
+    b->sums = c.take<lk::PackSums>((size_t)T);
+    b->scan = c.take<lk::PackSums>((size_t)T + 1);
+    b->scratch = c.take<lk::PackSums>(lk::scan_scratch_count(T));
+    b->item_begin = c.take<int64_t>((size_t)T + 1);
+    return c.off;
+}
+
+// Pinned bytes of a geometry request's totals and tune table.
+constexpr size_t kSumBytes = 64;
+size_t geometry_sum_bytes() { return kSumBytes + (size_t)lk::kTuneClasses * lk::kTuneClasses * sizeof(int32_t); }
+
 size_t request_result_bytes(size_t P) {
     return ((P * 4 + 255) & ~(size_t)255) + ((P * 8 + 255) & ~(size_t)255) + ((P * 4 + 255) & ~(size_t)255) +
            256;   // the request's work counters
 }
+
+// Pinned host bytes of a geometry request's results: lk, raw, status,
+// counters, then its pair list.
+size_t geometry_host_bytes(size_t P) { return request_result_bytes(P) + P * 2 * sizeof(int32_t); }
 
 // Pinned host bytes of a request: its results, then its staged item tables.
 size_t request_host_bytes(const Packed& pk) {
@@ -1652,6 +1746,8 @@ struct lk_server {
     int num_sms = 1;
     cudaStream_t stream = nullptr;     // request setup and the bulk waves
     cudaStream_t finish = nullptr;     // each finished request's careful passes, FP64 fix, reduction, copies
+    cudaStream_t prep = nullptr;       // geometry requests' search and packing
+    Request* stalled = nullptr;        // the first geometry request of this step left waiting for room
     unsigned char* d_arena = nullptr;
     unsigned char* h_arena = nullptr;
     Arena dev, host;
@@ -1685,13 +1781,13 @@ lk_status srv_fail(lk_server* s, lk_status st, const std::string& m) {
                             std::string(#call) + ": " + cudaGetErrorString(e_));            \
     } while (0)
 
-lk::SweepArgs request_args(lk_ctx* ctx, Workspace& ws, const Packed& pk, int near_cap) {
+lk::SweepArgs request_args(lk_ctx* ctx, Workspace& ws, int64_t n_tasks, int64_t n_items, int near_cap) {
     lk::SweepArgs a{};
     a.tasks = ws.tasks.p;
     a.item_begin = ws.item_begin.p;
     a.item_task = ws.item_task.p;
-    a.n_items = pk.n_items;
-    a.n_tasks = (int64_t)pk.tasks.size();
+    a.n_items = n_items;
+    a.n_tasks = n_tasks;
     a.partial = ws.partial.p;
     a.item_counter = ws.counters.p + 4;
     a.overflow = ws.counters.p + 1;
@@ -1714,6 +1810,13 @@ lk::SweepArgs request_args(lk_ctx* ctx, Workspace& ws, const Packed& pk, int nea
     return a;
 }
 
+void take_counts(Request* r) {
+    r->n_tasks = (int64_t)r->pk.tasks.size();
+    r->n_items = r->pk.n_items;
+    r->n_acc_items = r->pk.n_acc_items;
+    r->n_chunks = r->pk.n_chunks;
+}
+
 // Retire finished waves (block on the oldest when `block`).
 lk_status retire(lk_server* s, bool block) {
     while (!s->waves.empty()) {
@@ -1731,6 +1834,8 @@ lk_status retire(lk_server* s, bool block) {
             s->st.careful_items += (int64_t)(uint32_t)r->h_counters[2];
             s->st.careful_chunks += (int64_t)(uint32_t)r->h_counters[5];
             s->dev.release(r->dev_off, r->dev_bytes);
+            if (r->blk_bytes) s->dev.release(r->blk_off, r->blk_bytes);
+            r->blk_bytes = 0;
             auto it = std::find(s->running.begin(), s->running.end(), r);
             if (it != s->running.end()) s->running.erase(it);
             s->st.completed += 1;
@@ -1743,15 +1848,242 @@ lk_status retire(lk_server* s, bool block) {
     return LK_OK;
 }
 
+// A geometry request that ends without waves (no candidate pairs, or an
+// error): release what it holds and report it done.
+void complete_now(lk_server* s, Request* r, lk_status error, const std::string& msg) {
+    if (r->scr_bytes) s->dev.release(r->scr_off, r->scr_bytes);
+    if (r->blk_bytes) s->dev.release(r->blk_off, r->blk_bytes);
+    if (r->dev_bytes) s->dev.release(r->dev_off, r->dev_bytes);
+    if (r->sum_bytes) s->host.release(r->sum_off, r->sum_bytes);
+    if (r->host_bytes) s->host.release(r->host_off, r->host_bytes);
+    r->scr_bytes = r->blk_bytes = r->dev_bytes = r->sum_bytes = r->host_bytes = 0;
+    r->error = error;
+    if (error != LK_OK) {
+        r->n_tasks = 0;
+        r->error_msg = msg;
+    }
+    r->state = kDone;
+    s->finished.push_back(r->ticket);
+    auto it = std::find(s->running.begin(), s->running.end(), r);
+    if (it != s->running.end()) s->running.erase(it);
+    s->st.completed += 1;
+}
+
+// Pinned result pointers of a request's host block (results, then for a
+// geometry request its pair list).
+void bind_results(lk_server* s, Request* r) {
+    const size_t P = (size_t)r->n_tasks;
+    unsigned char* hb = s->h_arena + r->host_off;
+    r->h_lk = reinterpret_cast<int32_t*>(hb);
+    r->h_raw = reinterpret_cast<double*>(hb + ((P * 4 + 255) & ~(size_t)255));
+    r->h_status = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(r->h_raw) + ((P * 8 + 255) & ~(size_t)255));
+    r->h_counters = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(r->h_status) +
+                                                          ((P * 4 + 255) & ~(size_t)255));
+    r->h_pairs = reinterpret_cast<int32_t*>(hb + request_result_bytes(P));
+}
+
+// Admission of a geometry request: the potential link search's count pass
+// and the scan of its counts on the preparation stream (after the work that
+// preceded the submit on the server's stream); the candidate count is read
+// back without waiting.  Returns false when the arena has no room yet.
+bool start_search(lk_server* s, Request* r, lk_status* err) {
+    lk_ctx* ctx = r->ctx;
+    const int64_t L = ctx->n_loops;
+    *err = LK_OK;
+    SearchBufs sb;
+    r->scr_bytes = search_layout(L, r->sweep, &sb, 0);
+    if (!s->dev.alloc(r->scr_bytes, &r->scr_off)) {
+        r->scr_bytes = 0;
+        return false;
+    }
+    r->sum_bytes = geometry_sum_bytes();
+    if (!s->host.alloc(r->sum_bytes, &r->sum_off)) {
+        s->dev.release(r->scr_off, r->scr_bytes);
+        r->scr_bytes = r->sum_bytes = 0;
+        return false;
+    }
+    search_layout(L, r->sweep, &sb, (uintptr_t)(s->d_arena + r->scr_off));
+    unsigned char* hb = s->h_arena + r->sum_off;
+    r->h_sum = reinterpret_cast<long long*>(hb);
+    cudaStream_t st = s->prep;
+    auto check = [&](cudaError_t e) {
+        if (e != cudaSuccess && *err == LK_OK) {
+            *err = LK_ERR_CUDA;
+            s->err = std::string("lk_server_step (search): ") + cudaGetErrorString(e);
+        }
+    };
+    check(cudaStreamWaitEvent(st, r->ev, 0));   // the submit's fence on the server's stream
+    if (r->tuned) {
+        int32_t* h_tune = reinterpret_cast<int32_t*>(hb + kSumBytes);
+        std::fill(h_tune, h_tune + lk::kTuneClasses * lk::kTuneClasses, 0);
+        for (const auto& kv : ctx->tune) {
+            const uint32_t rc = kv.first >> 8, cc = kv.first & 0xffu;
+            if (rc < (uint32_t)lk::kTuneClasses && cc < (uint32_t)lk::kTuneClasses)
+                h_tune[rc * lk::kTuneClasses + cc] = kv.second;
+        }
+        check(cudaMemcpyAsync(sb.tune, h_tune, (size_t)lk::kTuneClasses * lk::kTuneClasses * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, st));
+    }
+    lk::launch_pls_keys(ctx->d_aabb, L, sb.keys, st);
+    if (r->sweep) {
+        lk::launch_pls_sort(sb.keys, L, sb.order, lk::pls_sort_size(L), st);
+        lk::launch_pls_sweep_count(sb.keys, L, sb.order, sb.counts, st);
+    } else {
+        lk::launch_pls_count(sb.keys, L, sb.counts, st);
+    }
+    lk::launch_scan_counts(sb.counts, L, sb.offsets, sb.scan, st);
+    check(cudaMemcpyAsync(r->h_sum, sb.offsets + L, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    check(cudaGetLastError());
+    check(cudaEventRecord(r->ev, st));
+    return true;
+}
+
+// Advance geometry requests whose search or packing has finished on the
+// device (polled, never waited for).
+lk_status advance_geometry(lk_server* s) {
+    std::vector<Request*> todo;
+    s->stalled = nullptr;
+    for (Request* r : s->running)
+        if (r->state == kSearching || r->state == kPacking) todo.push_back(r);
+    for (Request* r : todo) {
+        const cudaError_t q = cudaEventQuery(r->ev);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return srv_fail(s, LK_ERR_CUDA, std::string("lk_server_step: ") + cudaGetErrorString(q));
+        lk_ctx* ctx = r->ctx;
+        const int64_t L = ctx->n_loops;
+        if (r->state == kSearching) {
+            const int64_t T = r->h_sum[0];
+            if (T == 0) {
+                complete_now(s, r, LK_OK, "");
+                continue;
+            }
+            if (T > (int64_t)INT32_MAX) {
+                complete_now(s, r, LK_ERR_ARG, "lk_server_submit_geometry: more than 2^31 candidate pairs");
+                continue;
+            }
+            PackBufs pb;
+            const size_t blk = pack_layout(T, &pb, 0), hbytes = geometry_host_bytes((size_t)T);
+            if (Arena::round(blk) > s->opt.arena_bytes || Arena::round(hbytes) > s->opt.host_bytes) {
+                complete_now(s, r, LK_ERR_OOM, "lk_server_submit_geometry: the candidate pairs exceed the server's arena");
+                continue;
+            }
+            if (!s->dev.alloc(blk, &r->blk_off)) {                     // wait for room
+                if (!s->stalled) s->stalled = r;
+                continue;
+            }
+            if (!s->host.alloc(hbytes, &r->host_off)) {
+                s->dev.release(r->blk_off, blk);
+                if (!s->stalled) s->stalled = r;
+                continue;
+            }
+            r->blk_bytes = blk;
+            r->host_bytes = hbytes;
+            r->n_tasks = T;
+            bind_results(s, r);
+            pack_layout(T, &pb, (uintptr_t)(s->d_arena + r->blk_off));
+            SearchBufs sb;
+            search_layout(L, r->sweep, &sb, (uintptr_t)(s->d_arena + r->scr_off));
+            const lk::PackParams P{ctx->d_V, ctx->d_R, ctx->d_offsets, r->tuned ? sb.tune : nullptr,
+                                   ctx->opt.accurate_threshold, ctx->opt.tile_rows, 0};
+            cudaStream_t st = s->prep;
+            const unsigned npk = lk::pls_sort_size(T);
+            if (r->sweep) {
+                LK_SRV_CUDA(s, cudaMemsetAsync(pb.keys, 0xff, (size_t)npk * sizeof(unsigned long long), st));
+                lk::launch_pls_sweep_write(sb.keys, L, sb.order, sb.offsets, pb.keys, T, st);
+                lk::launch_bitonic_sort(pb.keys, npk, st);
+                lk::launch_pls_unpack(pb.keys, T, pb.pairs, st);
+            } else {
+                lk::launch_pls_write(sb.keys, L, sb.offsets, pb.pairs, T, st);
+            }
+            lk::launch_pack_keys(pb.pairs, T, P, pb.keys, npk, st);
+            lk::launch_bitonic_sort(pb.keys, npk, st);
+            lk::launch_pack_tasks(pb.keys, pb.pairs, T, P, pb.tasks, pb.sums, pb.scan, pb.scratch, pb.item_begin, st);
+            LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_sum + 1, pb.scan + T, sizeof(lk::PackSums), cudaMemcpyDeviceToHost, st));
+            LK_SRV_CUDA(s, cudaGetLastError());
+            LK_SRV_CUDA(s, cudaEventRecord(r->ev, st));
+            r->d_pairs = pb.pairs;
+            r->ws.tasks.p = pb.tasks;
+            r->ws.tasks.cap = (size_t)T;
+            r->ws.item_begin.p = pb.item_begin;
+            r->ws.item_begin.cap = (size_t)T + 1;
+            r->state = kPacking;
+            continue;
+        }
+        // kPacking: the totals are in; lay out the work buffers and start.
+        lk::PackSums tot;
+        std::memcpy(&tot, r->h_sum + 1, sizeof tot);
+        const int64_t T = r->n_tasks;
+        if (tot.items > (int64_t)INT32_MAX * 16) {
+            complete_now(s, r, LK_ERR_ARG, "lk_server_submit_geometry: too many work items");
+            continue;
+        }
+        Workspace probe;
+        const size_t need = request_layout(T, tot.items, tot.chunks, false, s->opt.near_capacity, &probe, 0);
+        if (Arena::round(need) > s->opt.arena_bytes) {
+            complete_now(s, r, LK_ERR_OOM, "lk_server_submit_geometry: request larger than the server's arena");
+            continue;
+        }
+        if (!s->dev.alloc(need, &r->dev_off)) {                       // wait for room
+            if (!s->stalled) s->stalled = r;
+            continue;
+        }
+        r->dev_bytes = need;
+        r->n_items = tot.items;
+        r->n_acc_items = tot.acc_items;
+        r->n_chunks = tot.chunks;
+        request_layout(T, r->n_items, r->n_chunks, false, s->opt.near_capacity, &r->ws,
+                       (uintptr_t)(s->d_arena + r->dev_off));
+        s->dev.release(r->scr_off, r->scr_bytes);
+        s->host.release(r->sum_off, r->sum_bytes);
+        r->scr_bytes = r->sum_bytes = 0;
+        r->h_sum = nullptr;
+        cudaStream_t st = s->stream;
+        lk::launch_pack_item_task(r->ws.item_begin.p, T, r->n_items, r->ws.item_task.p, st);
+        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.counters.p, 0, 8 * sizeof(unsigned long long), st));
+        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.fix_acc.p, 0, T * sizeof(unsigned long long), st));
+        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.fp64_count.p, 0, T * sizeof(unsigned long long), st));
+        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.flags.p, 0, T * sizeof(int), st));
+        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.item_fix.p, 0, r->ws.item_fix.cap * sizeof(unsigned long long), st));
+        lk::launch_pair_frames(r->ws.tasks.p, T, ctx->d_aabb, st);
+        LK_SRV_CUDA(s, cudaGetLastError());
+        r->args = request_args(ctx, r->ws, T, r->n_items, s->opt.near_capacity);
+        r->state = kRunning;
+        r->next_item = 0;
+        s->st.candidate_pairs += T;
+    }
+    return LK_OK;
+}
+
 // Admit queued requests in arrival order while slots and arena space last.
 lk_status admit(lk_server* s) {
     while (!s->queue.empty() && (int)s->running.size() < s->opt.max_requests) {
         Request* r = s->queue.front();
         lk_ctx* ctx = r->ctx;
+        if (r->geometry) {
+            s->running.push_back(r);
+            s->queue.pop_front();
+            s->st.admitted += 1;
+            if (ctx->n_loops < 2) {
+                complete_now(s, r, LK_OK, "");
+                continue;
+            }
+            lk_status err = LK_OK;
+            if (!start_search(s, r, &err)) {
+                // no room yet: back to the head of the queue
+                s->running.pop_back();
+                s->queue.push_front(r);
+                s->st.admitted -= 1;
+                break;
+            }
+            if (err != LK_OK) return err;
+            r->state = kSearching;
+            continue;
+        }
         if (!r->packed) {
             lk_status st = pack_pairs(ctx, r->pairs.data(), (int64_t)(r->pairs.size() / 2), r->pk);
             if (st != LK_OK) return srv_fail(s, st, ctx->err);
             r->packed = true;
+            take_counts(r);
             Workspace probe;
             r->dev_bytes = request_layout(r->pk, s->opt.near_capacity, &probe, 0);
             r->host_bytes = request_host_bytes(r->pk);
@@ -1762,14 +2094,14 @@ lk_status admit(lk_server* s) {
             break;
         }
         request_layout(r->pk, s->opt.near_capacity, &r->ws, (uintptr_t)(s->d_arena + r->dev_off));
-        const size_t P = r->pk.tasks.size();
+        const size_t P = (size_t)r->n_tasks;
         unsigned char* hb = s->h_arena + r->host_off;
         r->h_lk = reinterpret_cast<int32_t*>(hb);
         r->h_raw = reinterpret_cast<double*>(hb + ((P * 4 + 255) & ~(size_t)255));
         r->h_status = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(r->h_raw) + ((P * 8 + 255) & ~(size_t)255));
         r->h_counters = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(r->h_status) +
                                                               ((P * 4 + 255) & ~(size_t)255));
-        r->args = request_args(ctx, r->ws, r->pk, s->opt.near_capacity);
+        r->args = request_args(ctx, r->ws, r->n_tasks, r->n_items, s->opt.near_capacity);
         // Stage the item tables in pinned memory so that their upload is truly
         // asynchronous (a pageable source would make the copy wait for the
         // waves already queued on the stream, serialising host and device).
@@ -1820,10 +2152,10 @@ lk_status launch_wave(lk_server* s) {
     for (Request* r : s->running) {
         if (r->state != kRunning || budget <= 0 || n_acc + n_fast + 2 > kMaxSegs) continue;
         ++touched;
-        const int64_t lo = r->next_item, hi = std::min<int64_t>(r->pk.n_items, lo + budget);
+        const int64_t lo = r->next_item, hi = std::min<int64_t>(r->n_items, lo + budget);
         // accurate items are [0, n_acc_items), fast items after them
-        const int64_t a_lo = lo, a_hi = std::min(hi, r->pk.n_acc_items);
-        const int64_t f_lo = std::max(lo, r->pk.n_acc_items), f_hi = hi;
+        const int64_t a_lo = lo, a_hi = std::min(hi, r->n_acc_items);
+        const int64_t f_lo = std::max(lo, r->n_acc_items), f_hi = hi;
         if (a_hi > a_lo) {
             segs[n_acc] = lk::WaveSeg{r->args, a_lo, acc_items};
             acc_items += a_hi - a_lo;
@@ -1836,7 +2168,7 @@ lk_status launch_wave(lk_server* s) {
         }
         budget -= hi - lo;
         r->next_item = hi;
-        if (hi >= r->pk.n_items) {
+        if (hi >= r->n_items) {
             r->state = kLaunched;
             completing.push_back(r);
         }
@@ -1866,7 +2198,7 @@ lk_status launch_wave(lk_server* s) {
         st = s->finish;
     }
     for (Request* r : completing) {
-        const bool fast = r->pk.n_items > r->pk.n_acc_items, acc = r->pk.n_acc_items > 0;
+        const bool fast = r->n_items > r->n_acc_items, acc = r->n_acc_items > 0;
         lk::launch_careful_chunks(r->args, fast, acc, s->num_sms * lk::careful_chunk_blocks_per_sm(), st);
         lk::launch_sweep_careful(r->args, fast, acc, s->num_sms * lk::sweep_careful_blocks_per_sm(), st);
         lk::launch_near_fix(r->args, s->num_sms * 4, st);
@@ -1877,14 +2209,16 @@ lk_status launch_wave(lk_server* s) {
         ra.fix_acc = r->ws.fix_acc.p;
         ra.item_fix = r->ws.item_fix.p;
         ra.flags = r->ws.flags.p;
-        ra.n_tasks = (int64_t)r->pk.tasks.size();
+        ra.n_tasks = r->n_tasks;
         ra.int_tol = r->ctx->opt.int_tol;
         ra.lk_out = r->ws.lk.p;
         ra.raw_out = r->ws.raw.p;
         ra.status_out = r->ws.status.p;
         lk::launch_reduce(ra, st);
-        const size_t P = r->pk.tasks.size();
+        const size_t P = (size_t)r->n_tasks;
         LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_lk, r->ws.lk.p, P * 4, cudaMemcpyDeviceToHost, st));
+        if (r->geometry)
+            LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_pairs, r->d_pairs, P * 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_raw, r->ws.raw.p, P * 8, cudaMemcpyDeviceToHost, st));
         LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_status, r->ws.status.p, P * 4, cudaMemcpyDeviceToHost, st));
         LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_counters, r->ws.counters.p, 8 * sizeof(unsigned long long),
@@ -1930,6 +2264,7 @@ lk_status lk_server_create(lk_server** out, const lk_server_options* opt) {
     cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->finish, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->prep, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_arena, o.arena_bytes);
     if (e == cudaSuccess) e = cudaHostAlloc(&s->h_arena, o.host_bytes, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_counters, 2 * kWaveSlots * sizeof(unsigned long long));
@@ -1977,6 +2312,7 @@ lk_status lk_server_submit(lk_server* s, lk_ctx* ctx, const int32_t* loop_pairs,
         return srv_fail(s, st, ctx->err);
     }
     r->packed = true;
+    take_counts(r);
     Workspace probe;
     r->dev_bytes = request_layout(r->pk, s->opt.near_capacity, &probe, 0);
     r->host_bytes = request_host_bytes(r->pk);
@@ -1992,13 +2328,76 @@ lk_status lk_server_submit(lk_server* s, lk_ctx* ctx, const int32_t* loop_pairs,
     return LK_OK;
 }
 
+lk_status lk_server_submit_geometry(lk_server* s, lk_ctx* ctx, int64_t* ticket) {
+    if (!s) return srv_fail(nullptr, LK_ERR_ARG, "lk_server_submit_geometry: NULL server");
+    if (!ctx || !ticket) return srv_fail(s, LK_ERR_ARG, "lk_server_submit_geometry: invalid arguments");
+    if (ctx->opt.precision != LK_MIXED)
+        return srv_fail(s, LK_ERR_ARG, "lk_server_submit_geometry: the server runs the mixed-precision path");
+    if (ctx->n_loops > (int64_t)1 << 30) return srv_fail(s, LK_ERR_ARG, "lk_server_submit_geometry: too many loops");
+    if ((int64_t)s->queue.size() >= s->opt.max_queue)
+        return srv_fail(s, LK_ERR_BUSY, "lk_server_submit_geometry: queue full");
+    const int64_t L = ctx->n_loops;
+    Request* r = new Request();
+    r->ctx = ctx;
+    r->geometry = true;
+    r->packed = true;
+    // the same choice of search as lk_candidates
+    r->sweep = L * (L - 1) / 2 > ((int64_t)1 << 27);
+    r->tuned = ctx->opt.tile_rows <= 0 && !ctx->tune.empty();
+    SearchBufs sb;
+    if (Arena::round(search_layout(std::max<int64_t>(L, 1), r->sweep, &sb, 0)) > s->opt.arena_bytes ||
+        Arena::round(geometry_sum_bytes()) > s->opt.host_bytes) {
+        delete r;
+        return srv_fail(s, LK_ERR_OOM, "lk_server_submit_geometry: the search alone exceeds the server's arena");
+    }
+    // The search reads the context's boxes after the work enqueued on the
+    // server's stream so far (an lk_update there, say).
+    if (cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(r->ev, s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        delete r;
+        return srv_fail(s, LK_ERR_CUDA, "lk_server_submit_geometry: cannot record the request's fence");
+    }
+    r->ticket = s->next_ticket++;
+    s->queue.push_back(r);
+    s->all[r->ticket] = r;
+    s->st.submitted += 1;
+    s->st.geometry_requests += 1;
+    *ticket = r->ticket;
+    return LK_OK;
+}
+
 lk_status lk_server_step(lk_server* s, int wait) {
     if (!s) return srv_fail(nullptr, LK_ERR_ARG, "lk_server_step: NULL server");
     lk_status st = retire(s, false);
     if (st != LK_OK) return st;
+    if ((st = advance_geometry(s)) != LK_OK) return st;
     if ((st = admit(s)) != LK_OK) return st;
     if ((st = launch_wave(s)) != LK_OK) return st;
+    if (s->stalled && s->waves.empty()) {
+        // Nothing in flight will release memory: the geometry requests holding
+        // the arena wait on one another.  The oldest waiting one gives up.
+        bool busy = false;
+        for (Request* r : s->running) {
+            if (r->state == kRunning || r->state == kLaunched) busy = true;
+            if ((r->state == kSearching || r->state == kPacking) && cudaEventQuery(r->ev) == cudaErrorNotReady) busy = true;
+        }
+        cudaGetLastError();
+        if (!busy)
+            complete_now(s, s->stalled, LK_ERR_OOM,
+                         "lk_server_submit_geometry: no arena room while the other geometry requests hold it");
+        s->stalled = nullptr;
+    }
     if (wait && !s->waves.empty() && (st = retire(s, true)) != LK_OK) return st;
+    if (wait && s->waves.empty()) {
+        // nothing in flight but geometry requests' search or packing: wait for the oldest
+        for (Request* r : s->running)
+            if ((r->state == kSearching || r->state == kPacking) && r != s->stalled) {
+                const cudaError_t e = cudaEventSynchronize(r->ev);
+                if (e != cudaSuccess) return srv_fail(s, LK_ERR_CUDA, std::string("lk_server_step: ") + cudaGetErrorString(e));
+                break;
+            }
+    }
     return LK_OK;
 }
 
@@ -2021,8 +2420,9 @@ lk_status lk_server_poll(lk_server* s, int64_t ticket, int* done, int32_t* lk_ou
     auto it = s->all.find(ticket);
     if (it == s->all.end()) return srv_fail(s, LK_ERR_ARG, "lk_server_poll: unknown ticket");
     Request* r = it->second;
+    if (r->geometry) return srv_fail(s, LK_ERR_ARG, "lk_server_poll: a geometry request is polled by lk_server_poll_pairs");
     if (r->state != kDone) return LK_OK;
-    const size_t P = r->pk.tasks.size();
+    const size_t P = (size_t)r->n_tasks;
     // The pinned buffers are indexed by the caller's pair order already (the
     // reduction writes through out_index).
     if (lk_out) std::memcpy(lk_out, r->h_lk, P * 4);
@@ -2032,6 +2432,38 @@ lk_status lk_server_poll(lk_server* s, int64_t ticket, int* done, int32_t* lk_ou
     s->all.erase(it);
     delete r;
     *done = 1;
+    return LK_OK;
+}
+
+lk_status lk_server_poll_pairs(lk_server* s, int64_t ticket, int* done, int64_t* n_pairs, int32_t* pairs_out,
+                               int64_t capacity, int32_t* lk_out, double* raw_out, int32_t* status_out) {
+    if (!s || !done || !n_pairs || capacity < 0) return srv_fail(s, LK_ERR_ARG, "lk_server_poll_pairs: invalid arguments");
+    *done = 0;
+    *n_pairs = 0;
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return srv_fail(s, LK_ERR_ARG, "lk_server_poll_pairs: unknown ticket");
+    Request* r = it->second;
+    if (r->state != kDone) return LK_OK;
+    *done = 1;
+    const lk_status err = r->error;
+    if (err != LK_OK) {
+        const std::string msg = r->error_msg;
+        s->all.erase(it);
+        delete r;
+        return srv_fail(s, err, msg);
+    }
+    const size_t P = (size_t)r->n_tasks;
+    *n_pairs = (int64_t)P;
+    if ((int64_t)P > capacity) return LK_OK;   // the ticket stays valid for a larger buffer
+    if (P > 0) {
+        if (pairs_out) std::memcpy(pairs_out, r->geometry ? r->h_pairs : r->pairs.data(), P * 2 * sizeof(int32_t));
+        if (lk_out) std::memcpy(lk_out, r->h_lk, P * 4);
+        if (raw_out) std::memcpy(raw_out, r->h_raw, P * 8);
+        if (status_out) std::memcpy(status_out, r->h_status, P * 4);
+    }
+    if (r->host_bytes) s->host.release(r->host_off, r->host_bytes);
+    s->all.erase(it);
+    delete r;
     return LK_OK;
 }
 
@@ -2054,6 +2486,7 @@ void lk_server_destroy(lk_server* s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->finish) cudaStreamSynchronize(s->finish);
+    if (s->prep) cudaStreamSynchronize(s->prep);
     for (Wave& w : s->waves) {
         cudaEventDestroy(w.done);
         if (w.swept) cudaEventDestroy(w.swept);
@@ -2068,6 +2501,7 @@ void lk_server_destroy(lk_server* s) {
     if (s->h_arena) cudaFreeHost(s->h_arena);
     if (s->stream) cudaStreamDestroy(s->stream);
     if (s->finish) cudaStreamDestroy(s->finish);
+    if (s->prep) cudaStreamDestroy(s->prep);
     delete s;
 }
 

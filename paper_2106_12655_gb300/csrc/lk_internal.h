@@ -272,6 +272,34 @@ void launch_pls_unpack(const unsigned long long* keys, int64_t n, int32_t* pairs
 void launch_pls_count(const long long* keys, int64_t n_loops, int32_t* counts, cudaStream_t s);
 void launch_pls_write(const long long* keys, int64_t n_loops, const int64_t* offsets, int32_t* pairs,
                       int64_t capacity, cudaStream_t s);
+// Device-side packing of a pair list that lives on the device (lk_pack.cu).
+constexpr int kTuneClasses = 41;   // size classes ceil(log2 n) 0..40 per loop
+struct PackParams {
+    const Vtx* V;
+    const float4* R;
+    const int64_t* offsets;        // [n_loops + 1] first vertex of each loop
+    const int32_t* tune;           // [kTuneClasses^2] tile rows per (row, column) size class, 0 = none; or null
+    int64_t accurate_threshold;    // segment pairs from which a pair takes the accurate variant
+    int32_t user_rows;             // fixed tile rows (> 0), else the tune table or the default
+    int32_t pad;
+};
+struct PackSums {
+    long long items, chunks, acc_items, segment_pairs;
+};
+// Entries of the scratch a scan of n values takes (block totals, grand total).
+size_t scan_scratch_count(int64_t n);
+// offsets[0..n] = exclusive scan of counts[0..n-1] (total at [n]).
+void launch_scan_counts(const int32_t* counts, int64_t n, int64_t* offsets, long long* scratch, cudaStream_t s);
+// keys[0..npk) = (sort key << 32 | k) of pair k < n, ~0 above (npk = pls_sort_size(n)).
+void launch_pack_keys(const int32_t* pairs, int64_t n, const PackParams& P, unsigned long long* keys, unsigned npk,
+                      cudaStream_t s);
+// From the sorted keys: tasks[0..n), their counts (sums), the exclusive scan
+// of the counts (scan_out[0..n], totals at [n]) and item_begin[0..n].
+void launch_pack_tasks(const unsigned long long* keys, const int32_t* pairs, int64_t n, const PackParams& P,
+                       PairTask* tasks, PackSums* sums, PackSums* scan_out, PackSums* scratch, int64_t* item_begin,
+                       cudaStream_t s);
+void launch_pack_item_task(const int64_t* item_begin, int64_t n_tasks, int64_t n_items, int32_t* item_task,
+                           cudaStream_t s);
 int sweep_f64_blocks_per_sm();
 int sweep_careful_blocks_per_sm();
 

@@ -1,0 +1,277 @@
+// Device-side work packing for requests that carry geometry only: the pairs
+// come from the potential link search (Sec. 3.2, Algorithm 2) on the device,
+// and are laid out as work items on the device, so that no pair list passes
+// through the host.
+//
+// The layout is the one the host packer gives the same list (a pair's tiling
+// depends only on its two loop sizes and the tune table; accurate-variant
+// pairs first, then within each variant the largest items first, ties in list
+// order), computed as:
+//   1. per pair its orientation, tile height, items and a 64-bit sort key
+//      (variant, inverse item cost, list index);
+//   2. a bitonic sort of the keys;
+//   3. per sorted position its PairTask and its counts (items, 32-row chunks,
+//      accurate items, segment pairs);
+//   4. an exclusive scan of the counts (item_begin; the totals come last);
+//   5. per work item its task, by binary search in item_begin.
+// The scans here are plain three-pass block scans (block totals, one block
+// over the totals, block-local scan plus the block's offset), with 64-bit
+// sums, in a fixed order.
+#include <algorithm>
+
+#include "lk_internal.h"
+
+namespace lk {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;
+constexpr int kScanBlock = kScanThreads * kScanPer;   // elements per block
+
+__device__ __forceinline__ PackSums operator+(const PackSums& x, const PackSums& y) {
+    return PackSums{x.items + y.items, x.chunks + y.chunks, x.acc_items + y.acc_items,
+                    x.segment_pairs + y.segment_pairs};
+}
+__device__ __forceinline__ void zero(long long& v) { v = 0; }
+__device__ __forceinline__ void zero(PackSums& v) { v = PackSums{0, 0, 0, 0}; }
+__device__ __forceinline__ long long load(const int32_t* in, int64_t i) { return (long long)in[i]; }
+__device__ __forceinline__ PackSums load(const PackSums* in, int64_t i) { return in[i]; }
+
+// Exclusive scan of the block's thread sums in shared memory; returns the
+// block's total.
+template <class T>
+__device__ T block_exclusive(T& v, T* sh) {
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int d = 1; d < kScanThreads; d <<= 1) {
+        T add;
+        zero(add);
+        if (t >= d) add = sh[t - d];
+        __syncthreads();
+        if (t >= d) sh[t] = sh[t] + add;
+        __syncthreads();
+    }
+    const T total = sh[kScanThreads - 1];
+    T ex;
+    zero(ex);
+    if (t > 0) ex = sh[t - 1];
+    __syncthreads();
+    v = ex;
+    return total;
+}
+
+template <class T, class In>
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const In* __restrict__ in, int64_t n,
+                                                                   T* __restrict__ block_sums) {
+    __shared__ T sh[kScanThreads];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanPer;
+    T v;
+    zero(v);
+    for (int k = 0; k < kScanPer; ++k)
+        if (base + k < n) v = v + load(in, base + k);
+    const T total = block_exclusive(v, sh);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of the block totals in place, the grand total at [nb].
+template <class T>
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(T* __restrict__ block_sums, int64_t nb) {
+    __shared__ T sh[kScanThreads];
+    T carry;
+    zero(carry);
+    for (int64_t b0 = 0; b0 < nb; b0 += kScanBlock) {
+        const int64_t base = b0 + (int64_t)threadIdx.x * kScanPer;
+        T loc[kScanPer];
+        T v;
+        zero(v);
+        for (int k = 0; k < kScanPer; ++k) {
+            zero(loc[k]);
+            if (base + k < nb) loc[k] = block_sums[base + k];
+            v = v + loc[k];
+        }
+        const T total = block_exclusive(v, sh);
+        T run = carry + v;
+        for (int k = 0; k < kScanPer; ++k) {
+            if (base + k < nb) block_sums[base + k] = run;
+            run = run + loc[k];
+        }
+        carry = carry + total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) block_sums[nb] = carry;
+}
+
+template <class T, class In>
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const In* __restrict__ in, int64_t n,
+                                                                  const T* __restrict__ block_sums,
+                                                                  int64_t nb, T* __restrict__ out) {
+    __shared__ T sh[kScanThreads];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanPer;
+    T loc[kScanPer];
+    T v;
+    zero(v);
+    for (int k = 0; k < kScanPer; ++k) {
+        zero(loc[k]);
+        if (base + k < n) loc[k] = load(in, base + k);
+        v = v + loc[k];
+    }
+    block_exclusive(v, sh);
+    T run = block_sums[blockIdx.x] + v;
+    for (int k = 0; k < kScanPer; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run = run + loc[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = block_sums[nb];
+}
+
+template <class T, class In>
+void scan(const In* in, int64_t n, T* out, T* scratch, cudaStream_t s) {
+    const int64_t nb = std::max<int64_t>(1, (n + kScanBlock - 1) / kScanBlock);
+    scan_reduce_kernel<T, In><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, scratch);
+    scan_blocks_kernel<T><<<1, kScanThreads, 0, s>>>(scratch, nb);
+    scan_apply_kernel<T, In><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, scratch, nb, out);
+}
+
+struct Shape {
+    int32_t row_loop, col_loop, n_rows, n_cols, tile_rows, col_tiles, accurate;
+    int64_t items, chunks;
+    uint32_t key;
+};
+
+__device__ __forceinline__ uint32_t ceil_log2(int64_t v) {
+    uint32_t b = 0;
+    while (((int64_t)1 << b) < v) ++b;
+    return b;
+}
+
+// The shape of pair (a, b), as the host packer computes it.
+__device__ Shape pair_shape(const PackParams& P, int32_t a, int32_t b) {
+    Shape t;
+    const int64_t tc = kTileCols;
+    const int64_t na = P.offsets[a + 1] - P.offsets[a];
+    const int64_t nb = P.offsets[b + 1] - P.offsets[b];
+    // the orientation that sweeps fewer cells including the last column
+    // tile's padding; on a tie the longer loop is the row loop
+    const int64_t cells_a_rows = na * ((nb + tc - 1) / tc);
+    const int64_t cells_b_rows = nb * ((na + tc - 1) / tc);
+    const bool a_rows = cells_a_rows != cells_b_rows ? cells_a_rows < cells_b_rows : na >= nb;
+    t.row_loop = a_rows ? a : b;
+    t.col_loop = a_rows ? b : a;
+    const int64_t nr = a_rows ? na : nb, ncl = a_rows ? nb : na;
+    t.n_rows = (int32_t)nr;
+    t.n_cols = (int32_t)ncl;
+    int64_t rows = P.user_rows;
+    if (rows <= 0 && P.tune) {
+        const uint32_t rc = ceil_log2(nr), cc = ceil_log2(ncl);
+        if (rc < kTuneClasses && cc < kTuneClasses) rows = P.tune[rc * kTuneClasses + cc];
+    }
+    if (rows <= 0) {
+        const int64_t col_tiles = (ncl + tc - 1) / tc;
+        int64_t row_tiles = (nr + 255) / 256;
+        const int64_t max_items = 1 << 16;
+        if (col_tiles * row_tiles > max_items) row_tiles = max_items / col_tiles > 1 ? max_items / col_tiles : 1;
+        rows = (nr + row_tiles - 1) / row_tiles;
+        rows = (rows + kChunkRows - 1) / kChunkRows * kChunkRows;
+        if (rows > (int64_t)INT32_MAX) rows = INT32_MAX;
+    }
+    t.tile_rows = (int32_t)rows;
+    t.col_tiles = (int32_t)((ncl + tc - 1) / tc);
+    t.items = (int64_t)t.col_tiles * ((nr + rows - 1) / rows);
+    t.accurate = nr * ncl >= P.accurate_threshold ? 1 : 0;
+    const int64_t cost = (rows < nr ? rows : nr) * (tc < ncl ? tc : ncl);
+    const uint32_t c = (uint32_t)(cost < 0x7ffffffe ? cost : 0x7ffffffe);
+    t.key = (t.accurate ? 0u : 0x80000000u) | (0x7ffffffeu - c);
+    const int64_t full = nr / rows, last = nr - full * rows;
+    const int64_t per_col = full * ((rows + kChunkRows - 1) / kChunkRows) +
+                            (last > 0 ? (last + kChunkRows - 1) / kChunkRows : 0);
+    t.chunks = per_col * t.col_tiles;
+    return t;
+}
+
+__global__ void pack_keys_kernel(const int32_t* __restrict__ pairs, int64_t n, PackParams P, unsigned npk,
+                                 unsigned long long* __restrict__ keys) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npk) return;
+    if (k >= n) {
+        keys[k] = ~0ull;
+        return;
+    }
+    const Shape t = pair_shape(P, pairs[2 * k], pairs[2 * k + 1]);
+    keys[k] = ((unsigned long long)t.key << 32) | (unsigned long long)k;
+}
+
+__global__ void pack_tasks_kernel(const unsigned long long* __restrict__ keys, const int32_t* __restrict__ pairs,
+                                  int64_t n, PackParams P, PairTask* __restrict__ tasks,
+                                  PackSums* __restrict__ sums) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int32_t p = (int32_t)(keys[k] & 0xffffffffu);
+    const Shape t = pair_shape(P, pairs[2 * p], pairs[2 * p + 1]);
+    PairTask q{};
+    q.V = P.V;
+    q.R = P.R;
+    q.row_loop = t.row_loop;
+    q.col_loop = t.col_loop;
+    q.row_base = P.offsets[t.row_loop];
+    q.col_base = P.offsets[t.col_loop];
+    q.n_rows = t.n_rows;
+    q.n_cols = t.n_cols;
+    q.tile_rows = t.tile_rows;
+    q.col_tiles = t.col_tiles;
+    q.out_index = p;
+    q.status = 0;
+    q.accurate = t.accurate;
+    q.scale = 1.0f;
+    tasks[k] = q;
+    sums[k] = PackSums{t.items, t.chunks, t.accurate ? t.items : 0, (long long)t.n_rows * t.n_cols};
+}
+
+__global__ void pack_item_begin_kernel(const PackSums* __restrict__ scan, int64_t n, int64_t* __restrict__ item_begin) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k <= n) item_begin[k] = scan[k].items;
+}
+
+// item_task[i] = the task k with item_begin[k] <= i < item_begin[k + 1].
+__global__ void pack_item_task_kernel(const int64_t* __restrict__ item_begin, int64_t n_tasks, int64_t n_items,
+                                      int32_t* __restrict__ item_task) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_items) return;
+    int64_t lo = 0, hi = n_tasks - 1;   // the last k with item_begin[k] <= i
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (item_begin[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    item_task[i] = (int32_t)lo;
+}
+
+}  // namespace
+
+size_t scan_scratch_count(int64_t n) { return (size_t)std::max<int64_t>(1, (n + kScanBlock - 1) / kScanBlock) + 1; }
+
+void launch_scan_counts(const int32_t* counts, int64_t n, int64_t* offsets, long long* scratch, cudaStream_t s) {
+    scan<long long, int32_t>(counts, n, reinterpret_cast<long long*>(offsets), scratch, s);
+}
+
+void launch_pack_keys(const int32_t* pairs, int64_t n, const PackParams& P, unsigned long long* keys, unsigned npk,
+                      cudaStream_t s) {
+    pack_keys_kernel<<<(npk + 255) / 256, 256, 0, s>>>(pairs, n, P, npk, keys);
+}
+
+void launch_pack_tasks(const unsigned long long* keys, const int32_t* pairs, int64_t n, const PackParams& P,
+                       PairTask* tasks, PackSums* sums, PackSums* scan_out, PackSums* scratch, int64_t* item_begin,
+                       cudaStream_t s) {
+    if (n <= 0) return;
+    pack_tasks_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, pairs, n, P, tasks, sums);
+    scan<PackSums, PackSums>(sums, n, scan_out, scratch, s);
+    pack_item_begin_kernel<<<(unsigned)((n + 256) / 256), 256, 0, s>>>(scan_out, n, item_begin);
+}
+
+void launch_pack_item_task(const int64_t* item_begin, int64_t n_tasks, int64_t n_items, int32_t* item_task,
+                           cudaStream_t s) {
+    if (n_items <= 0 || n_tasks <= 0) return;
+    pack_item_task_kernel<<<(unsigned)((n_items + 255) / 256), 256, 0, s>>>(item_begin, n_tasks, n_items, item_task);
+}
+
+}  // namespace lk

@@ -41,7 +41,8 @@ STATUS_NAMES = {0: "LK_OK", 1: "LK_ERR_ARG", 2: "LK_ERR_ZERO_SEGMENT", 3: "LK_ER
 EXPORTED = ["lk_default_options", "lk_create", "lk_update", "lk_verify", "lk_sync", "lk_get_stats", "lk_get_options",
             "lk_destroy", "lk_last_error", "lk_plan_create", "lk_plan_run", "lk_plan_destroy",
             "lk_verify_noalloc", "lk_verify_expected", "lk_autotune", "lk_tune_get", "lk_tune_set", "lk_server_default_options", "lk_server_create", "lk_server_stream",
-            "lk_server_submit", "lk_server_step", "lk_server_poll", "lk_server_completed",
+            "lk_server_submit", "lk_server_submit_geometry", "lk_server_step", "lk_server_poll",
+            "lk_server_poll_pairs", "lk_server_completed",
             "lk_server_get_stats", "lk_server_last_error", "lk_server_destroy", "lk_candidates"]
 
 
@@ -74,7 +75,8 @@ class lk_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "queued", "running",
                                                "waves", "waves_in_flight", "items_launched",
                                                "max_requests_per_wave", "arena_used", "near_overflow",
-                                               "careful_items", "careful_chunks")]
+                                               "careful_items", "careful_chunks", "geometry_requests",
+                                               "candidate_pairs")]
 
 
 class LkError(RuntimeError):
@@ -137,6 +139,11 @@ def load(path: str | None = None):
     lib.lk_server_stream.argtypes = [vp]
     lib.lk_server_submit.restype = ctypes.c_int
     lib.lk_server_submit.argtypes = [vp, vp, i32p, i64, ctypes.POINTER(ctypes.c_int64)]
+    lib.lk_server_submit_geometry.restype = ctypes.c_int
+    lib.lk_server_submit_geometry.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.lk_server_poll_pairs.restype = ctypes.c_int
+    lib.lk_server_poll_pairs.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64), vp,
+                                         i64, vp, vp, vp]
     lib.lk_server_step.restype = ctypes.c_int
     lib.lk_server_step.argtypes = [vp, ctypes.c_int]
     lib.lk_server_poll.restype = ctypes.c_int
@@ -387,6 +394,23 @@ def lk_server_submit(srv, ctx, loop_pairs) -> int:
     return t.value
 
 
+def lk_server_submit_geometry(srv, ctx) -> int:
+    t = ctypes.c_int64()
+    _check_srv(load().lk_server_submit_geometry(srv, ctx, ctypes.byref(t)), srv)
+    return t.value
+
+
+def lk_server_poll_pairs(srv, ticket, pairs_out=None, lk_out=None, raw_out=None, status_out=None,
+                         capacity: int = 0):
+    """(done, n_pairs); the outputs are filled (and the ticket released) only
+    when capacity >= n_pairs."""
+    d = ctypes.c_int()
+    n = ctypes.c_int64()
+    _check_srv(load().lk_server_poll_pairs(srv, ticket, ctypes.byref(d), ctypes.byref(n), _ptr(pairs_out), capacity,
+                                           _ptr(lk_out), _ptr(raw_out), _ptr(status_out)), srv)
+    return bool(d.value), n.value
+
+
 def lk_server_step(srv, wait: bool = False):
     _check_srv(load().lk_server_step(srv, 1 if wait else 0), srv)
 
@@ -473,3 +497,17 @@ class Linker:
             self.close()
         except Exception:
             pass
+
+
+def server_take_pairs(srv, ticket):
+    """None while the request runs; then (pairs [n, 2], lk, raw, status), the
+    ticket released."""
+    done, n = lk_server_poll_pairs(srv, ticket)
+    if not done:
+        return None
+    pairs = np.zeros((n, 2), np.int32)
+    lk = np.zeros(n, np.int32)
+    raw = np.zeros(n, np.float64)
+    st = np.zeros(n, np.int32)
+    lk_server_poll_pairs(srv, ticket, pairs, lk, raw, st, capacity=n)
+    return pairs, lk, raw, st

@@ -7,6 +7,12 @@ receives a small displacement (lk_update) when none of its requests is in
 flight.  Latency is measured from a request's scheduled arrival to the moment
 lk_server_poll hands its results to the host.  All linking-number work runs in
 the library; this module only schedules submissions and reads clocks.
+
+Requests can also carry geometry only (mode "geometry"): verify every
+potential link of the pile's current geometry, the search and packing done on
+the device by lk_server_submit_geometry.  Mode "host_search" serves the same
+requests through a host round trip instead: lk_candidates on the server's
+stream (after the pile's update), then lk_server_submit of the list.
 """
 from __future__ import annotations
 
@@ -58,14 +64,23 @@ def request_plan(scenes, n_requests, seed=0, min_pairs=1000, max_pairs=20000):
     return plan
 
 
-def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0, max_outstanding=None):
+def geometry_plan(scenes, n_requests, seed=0):
+    """Whole-pile requests: (scene index, None) for each request."""
+    rng = np.random.default_rng(seed)
+    return [(int(rng.integers(len(scenes))), None) for _ in range(n_requests)]
+
+
+def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0, max_outstanding=None,
+        mode="pairs"):
     """Serve `plan`; arrivals are Poisson at rate_per_s (None: all at t = 0).
     With max_outstanding, a request is submitted only while fewer than that
     many are queued or running (a closed loop: with rate_per_s None this
     measures the sustained capacity, the host packing of later requests
-    overlapping the device work of earlier ones).  Returns per-request
-    latencies (s), the wall time, and the number of pair results whose status
-    was not LK_OK."""
+    overlapping the device work of earlier ones).  mode: "pairs" (each plan
+    entry carries its pair list), "geometry" or "host_search" (whole-pile
+    requests, see the module's head).  Returns per-request latencies (s), the
+    wall time, the number of pair results whose status was not LK_OK, and the
+    number of pairs verified."""
     rng = np.random.default_rng(seed)
     n = len(plan)
     if rate_per_s is None:
@@ -73,8 +88,13 @@ def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0
     else:
         arrivals = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
     stream = lk.lk_server_stream(srv)
-    status = np.zeros(max(p.shape[0] for _, p in plan), np.int32)
+    cap = max(p.shape[0] for _, p in plan) if mode == "pairs" else 0
+    if mode != "pairs":
+        cap = max(sc.geometry.pairs.shape[0] for sc in scenes) * 2 + 1024
+    status = np.zeros(cap, np.int32)
+    pairs_buf = np.zeros((cap, 2), np.int32)
     bad = 0
+    verified = 0
     pending = {}          # ticket -> (request index, scene index)
     lat = np.zeros(n)
     nxt = 0
@@ -90,7 +110,13 @@ def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0
             if update and sc.in_flight == 0:
                 lk.lk_update(sc.ctx, sc.delta_neg if sc.flip else sc.delta_pos, True, stream)
                 sc.flip = not sc.flip
-            t = lk.lk_server_submit(srv, sc.ctx, pairs)
+            if mode == "geometry":
+                t = lk.lk_server_submit_geometry(srv, sc.ctx)
+            elif mode == "host_search":
+                m = lk.lk_candidates(sc.ctx, pairs_buf, stream)
+                t = lk.lk_server_submit(srv, sc.ctx, pairs_buf[:min(m, cap)])
+            else:
+                t = lk.lk_server_submit(srv, sc.ctx, pairs)
             sc.in_flight += 1
             pending[t] = (nxt, k)
             nxt += 1
@@ -98,9 +124,13 @@ def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0
             lk.lk_server_step(srv, wait=False)
         lk.lk_server_step(srv, wait=False)
         for t in lk.lk_server_completed(srv):
-            if lk.lk_server_poll(srv, t, None, None, status):
+            got, m = lk.lk_server_poll_pairs(srv, t, None, None, None, status, capacity=cap)
+            if got:
+                if m > cap:
+                    raise RuntimeError("a request returned more pairs than the driver's buffer")
                 i, k = pending.pop(t)
-                bad += int(np.count_nonzero(status[:plan[i][1].shape[0]]))
+                bad += int(np.count_nonzero(status[:m]))
+                verified += m
                 lat[i] = (time.perf_counter() - t0) - arrivals[i]
                 scenes[k].in_flight -= 1
                 done += 1
@@ -109,7 +139,7 @@ def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0
             if wait > 0:
                 time.sleep(min(wait, 0.001))
     wall = time.perf_counter() - t0
-    return lat, wall, bad
+    return lat, wall, bad, verified
 
 
 def plan_sizes(scenes, plan):
