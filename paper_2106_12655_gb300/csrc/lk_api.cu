@@ -1621,6 +1621,8 @@ struct Wave {
 constexpr int kWaveSlots = 3;          // waves in flight at most
 constexpr int kMaxSegs = 256;          // request runs per wave
 
+constexpr int64_t kServerMaxChunks = (int64_t)1 << 22;
+
 // Carve one request's work buffers out of the arena at `base` (or, with
 // base = 0, only measure them); returns the bytes used.  Without `tables` the
 // pair tasks and item_begin live elsewhere (a geometry request's pack block).
@@ -1642,7 +1644,10 @@ size_t request_layout(int64_t n_tasks, int64_t n_items, int64_t n_chunks, bool t
     bind(ws->item_task, I);
     bind(ws->partial, I);
     bind(ws->careful_items, I);
-    bind(ws->careful_chunks, (size_t)std::max<int64_t>(1, std::min<int64_t>(n_chunks, (int64_t)1 << 16)));
+    // room for every chunk of the request (up to 2^22 entries, 64 MB): a full
+    // list hands items over whole, whose careful re-sum rounds differently,
+    // so a result would depend on which items found the list full
+    bind(ws->careful_chunks, (size_t)std::max<int64_t>(1, std::min<int64_t>(n_chunks, kServerMaxChunks)));
     bind(ws->item_fix, I);
     bind(ws->near_list, (size_t)near_cap);
     bind(ws->fix_acc, P);

@@ -509,5 +509,6 @@ def server_take_pairs(srv, ticket):
     lk = np.zeros(n, np.int32)
     raw = np.zeros(n, np.float64)
     st = np.zeros(n, np.int32)
-    lk_server_poll_pairs(srv, ticket, pairs, lk, raw, st, capacity=n)
+    if n > 0:            # with no pairs the first call has released the ticket
+        lk_server_poll_pairs(srv, ticket, pairs, lk, raw, st, capacity=n)
     return pairs, lk, raw, st
