@@ -444,6 +444,18 @@ const char* lk_server_last_error(const lk_server* srv);
 void lk_server_destroy(lk_server* srv);
 
 /*
+ * Measurement support (the paper has no counterpart): the FP32 peak of this
+ * GPU as the bulk sweep's roofline denominator, measured by a kernel of
+ * independent packed FP32x2 fused multiply-adds on every SM (eight chains per
+ * thread, 2,048 threads per SM), timed with CUDA events on `cuda_stream`
+ * (the fastest of three launches after one warm-up, about 16 ms each).
+ * *tflops receives the measured rate (2 flops per lane per FMA), *ms (may be
+ * NULL) one launch's time.  It allocates and frees a small device buffer.
+ * Errors: LK_ERR_ARG (tflops NULL), LK_ERR_OOM, LK_ERR_CUDA.
+ */
+lk_status lk_measure_fp32_peak(double* tflops, double* ms, void* cuda_stream);
+
+/*
  * Allocation-free verify (the paper has no counterpart; this is a service of
  * this library).  For callers that cannot allocate device memory at the time
  * they verify: a simulation step under a strict no-allocation rule (a device

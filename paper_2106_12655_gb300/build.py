@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "liblk.so")
-SOURCES = ["lk_kernels.cu", "lk_api.cu", "lk_pls.cu", "lk_pack.cu"]
+SOURCES = ["lk_kernels.cu", "lk_api.cu", "lk_pls.cu", "lk_pack.cu", "lk_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -42,7 +42,7 @@ EXPORTED = ["lk_default_options", "lk_create", "lk_update", "lk_verify", "lk_syn
             "lk_destroy", "lk_last_error", "lk_plan_create", "lk_plan_run", "lk_plan_destroy",
             "lk_verify_noalloc", "lk_verify_expected", "lk_autotune", "lk_tune_get", "lk_tune_set", "lk_server_default_options", "lk_server_create", "lk_server_stream",
             "lk_server_submit", "lk_server_submit_geometry", "lk_server_step", "lk_server_poll",
-            "lk_server_poll_pairs", "lk_server_completed",
+            "lk_server_poll_pairs", "lk_server_completed", "lk_measure_fp32_peak",
             "lk_server_get_stats", "lk_server_last_error", "lk_server_destroy", "lk_candidates"]
 
 
@@ -144,6 +144,8 @@ def load(path: str | None = None):
     lib.lk_server_poll_pairs.restype = ctypes.c_int
     lib.lk_server_poll_pairs.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64), vp,
                                          i64, vp, vp, vp]
+    lib.lk_measure_fp32_peak.restype = ctypes.c_int
+    lib.lk_measure_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     lib.lk_server_step.restype = ctypes.c_int
     lib.lk_server_step.argtypes = [vp, ctypes.c_int]
     lib.lk_server_poll.restype = ctypes.c_int
@@ -409,6 +411,16 @@ def lk_server_poll_pairs(srv, ticket, pairs_out=None, lk_out=None, raw_out=None,
     _check_srv(load().lk_server_poll_pairs(srv, ticket, ctypes.byref(d), ctypes.byref(n), _ptr(pairs_out), capacity,
                                            _ptr(lk_out), _ptr(raw_out), _ptr(status_out)), srv)
     return bool(d.value), n.value
+
+
+def lk_measure_fp32_peak(stream=None):
+    """(TFLOP/s, ms of one launch) of the packed FP32 FMA peak kernel."""
+    t = ctypes.c_double()
+    m = ctypes.c_double()
+    st = load().lk_measure_fp32_peak(ctypes.byref(t), ctypes.byref(m), _stream(stream))
+    if st != LK_OK:
+        raise LkError(st, "lk_measure_fp32_peak failed")
+    return t.value, m.value
 
 
 def lk_server_step(srv, wait: bool = False):
