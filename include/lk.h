@@ -444,13 +444,14 @@ const char* lk_server_last_error(const lk_server* srv);
 void lk_server_destroy(lk_server* srv);
 
 /*
- * Measurement support (the paper has no counterpart): the FP32 peak of this
- * GPU as the bulk sweep's roofline denominator, measured by a kernel of
- * independent packed FP32x2 fused multiply-adds on every SM (eight chains per
- * thread, 2,048 threads per SM), timed with CUDA events on `cuda_stream`
- * (the fastest of three launches after one warm-up, about 16 ms each).
- * *tflops receives the measured rate (2 flops per lane per FMA), *ms (may be
- * NULL) one launch's time.  It allocates and frees a small device buffer.
+ * Measurement support (the paper has no counterpart): the FP32 rate this GPU
+ * reaches, reported beside the bulk sweep's roofline, measured by kernels of
+ * independent fused multiply-adds on every SM (packed FP32x2 with eight
+ * chains per thread, and scalar with sixteen; 2,048 threads per SM), timed
+ * with CUDA events on `cuda_stream`: the faster form, each the fastest of
+ * three launches after one warm-up (about 16-20 ms each).  *tflops receives
+ * the rate (2 flops per FMA and lane), *ms (may be NULL) that launch's time.
+ * It allocates and frees a small device buffer.
  * Errors: LK_ERR_ARG (tflops NULL), LK_ERR_OOM, LK_ERR_CUDA.
  */
 lk_status lk_measure_fp32_peak(double* tflops, double* ms, void* cuda_stream);
