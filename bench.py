@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--precise-only", action="store_true",
                     help="verify one woundball pair (nu = 10^3, 2 x 10^5 segments) twice, which the precise "
                          "variant sums: for profiling that kernel")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="the serving capacity alone (closed loop of 32, --serving-requests requests after 40 "
+                         "warm-up ones): for launch lists under a profiler")
     ap.add_argument("--headline-only", action="store_true",
                     help="time the headline step only (no tuning, FP64 baseline, end-to-end or other blocks): "
                          "for launch lists under a profiler")
@@ -1038,10 +1041,36 @@ def run_precise_only(args):
                       "error_estimate": float(est[0]), "precise_pairs": stats["precise_pairs"]}), flush=True)
 
 
+def run_serving_only(args):
+    """Closed-loop serving capacity on the six resident piles, alone."""
+    from paper_2106_12655_gb300 import build as B
+    from paper_2106_12655_gb300 import lk
+    from paper_2106_12655_gb300 import serving as S
+
+    B.build()
+    lk.load()
+    scenes = S.make_scenes(seed=5, n_scenes=6)
+    srv = lk.lk_server_create(None)
+    try:
+        S.run(srv, scenes, S.request_plan(scenes, 40, seed=99), None, max_outstanding=32)
+        plan = S.request_plan(scenes, args.serving_requests, seed=1)
+        lat, wall, bad, _ = S.run(srv, scenes, plan, None, max_outstanding=32)
+        pairs, sps = S.plan_sizes(scenes, plan)
+        print(json.dumps({"workload": "serving capacity, six chainmail piles, closed loop of 32",
+                          "n_requests": len(plan), "req_per_s": len(plan) / wall, "sp_per_s": float(sps.sum()) / wall,
+                          "nonok_pair_status": bad, "server_stats": lk.lk_server_get_stats(srv)}), flush=True)
+    finally:
+        lk.lk_server_destroy(srv)
+        S.close(scenes)
+
+
 def main():
     args = parse()
     if args.precise_only:
         run_precise_only(args)
+        return
+    if args.serving_only:
+        run_serving_only(args)
         return
     if args.impl == "reference":
         run_reference(args)
