@@ -673,6 +673,67 @@ def tuning_block(g, v, off, pairs_d, stream, flush, steps=20):
     return res, (table if res["use_tuned"] else None)
 
 
+def tuning_other_block(stream, reps=7):
+    """The autotuner on the knit yarn and on the six serving piles: one
+    lk_verify of every candidate pair (device lists and results, L2 flushed
+    before each, CUDA events, median of `reps` after one warm-up) with the
+    built-in work-item heights and with lk_autotune's table, and the largest
+    difference between the two tables' raw sums (the tables only reorder the
+    FP64 sums)."""
+    import torch
+    from paper_2106_12655_gb300 import lk
+    from paper_2106_12655_gb300 import serving as S
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(ctx, pairs_d, out):
+        ms = []
+        for k in range(reps + 1):
+            flush.fill_(k & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lk.lk_verify(ctx, pairs_d, *out, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if k:
+                ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    def compare(geoms):
+        res = {"default_ms": 0.0, "tuned_ms": 0.0, "tune_seconds": 0.0, "max_abs_raw_diff": 0.0, "tables": []}
+        for g in geoms:
+            v = torch.from_numpy(g.vertices).cuda()
+            off = torch.from_numpy(g.offsets).cuda()
+            pairs_d = torch.from_numpy(np.ascontiguousarray(g.pairs)).cuda()
+            n = g.pairs.shape[0]
+            raws = []
+            for label in ("default", "tuned"):
+                out = (torch.zeros(n, dtype=torch.int32, device="cuda"),
+                       torch.zeros(n, dtype=torch.float64, device="cuda"),
+                       torch.zeros(n, dtype=torch.int32, device="cuda"))
+                ctx = lk.lk_create(v, off, None, stream)
+                try:
+                    if label == "tuned":
+                        t0 = time.perf_counter()
+                        lk.lk_autotune(ctx, g.pairs, stream)
+                        res["tune_seconds"] += time.perf_counter() - t0
+                        res["tables"].append(lk.lk_tune_get(ctx).reshape(-1, 3).tolist())
+                    res[label + "_ms"] += timed(ctx, pairs_d, out)
+                    raws.append(out[1].cpu().numpy())
+                finally:
+                    lk.lk_destroy(ctx)
+            res["max_abs_raw_diff"] = max(res["max_abs_raw_diff"], float(np.max(np.abs(raws[0] - raws[1]))))
+        res["tuned_over_default"] = res["tuned_ms"] / res["default_ms"]
+        return res
+
+    from paper_2106_12655_gb300 import workloads as W
+
+    scenes = S.make_scenes(seed=5, n_scenes=6)       # the serving block's piles
+    piles = [sc.geometry for sc in scenes]
+    S.close(scenes)
+    return {"knit_yarn": compare([W.knit_yarn()]), "serving_piles": compare(piles)}
+
+
 def cpu_baseline(g):
     """The FP64 oracle on the sheet: every pair on all host cores (one pass),
     and a seeded 1/16 sample of the pairs on one core."""
@@ -943,6 +1004,7 @@ def run_ours(args):
     if not args.no_stress and world == 1:
         line["stress"] = stress_block(stream)
         line["configs"] = configs_block(stream)
+        line["tuning_other"] = tuning_other_block(stream)
     if not args.no_cpu_baseline and world == 1:
         ref_raw, cb = cpu_baseline(g)
         line["cpu_baseline"] = cb
@@ -990,6 +1052,10 @@ def summary(line):
                                        "p50_ms": [_g(x["p50_ms"]) for x in sg[m]["loads"]],
                                        "p99_ms": [_g(x["p99_ms"]) for x in sg[m]["loads"]]}
                                    for m in ("geometry", "host_search")}
+    if "tuning_other" in line:
+        out["tuned_over_default"] = {k: _g(v["tuned_over_default"]) for k, v in line["tuning_other"].items()}
+        out["tuned_over_default"]["sheet"] = _g(line["tuning"]["tuned_ms"] / line["tuning"]["default_ms"]) \
+            if "tuned_ms" in line.get("tuning", {}) else None
     if "configs" in line:
         c = line["configs"]
         err["ring_chain"] = _g(c["ring_chain"]["raw_err_vs_oracle"]["max"])
