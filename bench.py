@@ -192,13 +192,15 @@ def serving_block(args):
                "loads": []}
         for load in (0.5, 0.8, 0.95):
             plan = S.request_plan(scenes, args.serving_requests, seed=int(load * 100))
-            lat, wall, bad, _ = S.run(srv, scenes, plan, rate_per_s=load * cap, seed=int(load * 1000))
+            rec = {}
+            lat, wall, bad, _ = S.run(srv, scenes, plan, rate_per_s=load * cap, seed=int(load * 1000), record=rec)
             pairs, sps = S.plan_sizes(scenes, plan)
             out["loads"].append({"load": load, "offered_req_per_s": load * cap, "req_per_s": len(plan) / wall,
                                  "pairs_per_s": pairs.sum() / wall, "sp_per_s": sps.sum() / wall,
                                  "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                                  "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                                 "n_requests": len(plan), "nonok_pair_status": bad})
+                                 "n_requests": len(plan), "nonok_pair_status": bad,
+                                 "tail": tail_breakdown(lat, sps, rec)})
         out["server_stats"] = lk.lk_server_get_stats(srv)
         out["potential_link_search"] = pls_block(scenes)
         out["batched_same_piles"] = batched_piles_block(scenes)
@@ -206,6 +208,26 @@ def serving_block(args):
     finally:
         lk.lk_server_destroy(srv)
         S.close(scenes)
+
+
+def tail_breakdown(lat, sps, rec):
+    """Where the latency tail comes from: p50/p99 of the smallest and the
+    largest third of the requests (by segment pairs), of the requests that
+    found at most 2 / at least 8 others outstanding when they were submitted,
+    and the share of the p99-and-above requests that arrived behind 8 or more."""
+    lat = np.asarray(lat) * 1e3
+    depth = rec["depth"]
+    lo, hi = np.percentile(sps, [33.3, 66.7])
+    q99 = np.percentile(lat, 99)
+
+    def pct(mask):
+        return ({"n": int(mask.sum()), "p50_ms": float(np.percentile(lat[mask], 50)),
+                 "p99_ms": float(np.percentile(lat[mask], 99))} if mask.any() else {"n": 0})
+
+    return {"small_third": pct(sps <= lo), "large_third": pct(sps >= hi),
+            "depth_le_2": pct(depth <= 2), "depth_ge_8": pct(depth >= 8),
+            "p99_tail_behind_8_or_more": float(np.mean(depth[lat >= q99] >= 8)),
+            "mean_depth": float(depth.mean()), "max_submit_late_ms": 1e3 * float(np.max(rec["late"]))}
 
 
 def geometry_serving_block(args):

@@ -71,7 +71,7 @@ def geometry_plan(scenes, n_requests, seed=0):
 
 
 def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0, max_outstanding=None,
-        mode="pairs"):
+        mode="pairs", record=None):
     """Serve `plan`; arrivals are Poisson at rate_per_s (None: all at t = 0).
     With max_outstanding, a request is submitted only while fewer than that
     many are queued or running (a closed loop: with rate_per_s None this
@@ -80,7 +80,9 @@ def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0
     entry carries its pair list), "geometry" or "host_search" (whole-pile
     requests, see the module's head).  Returns per-request latencies (s), the
     wall time, the number of pair results whose status was not LK_OK, and the
-    number of pairs verified."""
+    number of pairs verified.  With `record` (a dict), it also receives per
+    request the requests outstanding when it was submitted ("depth") and the
+    delay between its scheduled arrival and its submission ("late", s)."""
     rng = np.random.default_rng(seed)
     n = len(plan)
     if rate_per_s is None:
@@ -97,6 +99,8 @@ def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0
     verified = 0
     pending = {}          # ticket -> (request index, scene index)
     lat = np.zeros(n)
+    depth = np.zeros(n, np.int64)
+    late = np.zeros(n)
     nxt = 0
     done = 0
     t0 = time.perf_counter()
@@ -118,6 +122,8 @@ def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0
             else:
                 t = lk.lk_server_submit(srv, sc.ctx, pairs)
             sc.in_flight += 1
+            depth[nxt] = len(pending)
+            late[nxt] = (time.perf_counter() - t0) - arrivals[nxt]
             pending[t] = (nxt, k)
             nxt += 1
             # launch work as soon as it is admitted, not after a burst of submits
@@ -139,6 +145,9 @@ def run(srv, scenes, plan, rate_per_s=None, seed=1, update=True, timeout_s=600.0
             if wait > 0:
                 time.sleep(min(wait, 0.001))
     wall = time.perf_counter() - t0
+    if record is not None:
+        record["depth"] = depth
+        record["late"] = late
     return lat, wall, bad, verified
 
 
