@@ -64,3 +64,30 @@ def test_tuning_cache_round_trip(tmp_path, monkeypatch):
     assert not tuning.restore("ctx-other", "another GPU", path)
     assert "ctx-other" not in installed
     assert not tuning.restore("ctx-x", "GB300 A", str(tmp_path / "missing.json"))
+
+
+def test_geometry_plan_whole_pile_requests():
+    scenes = _scenes([10, 20, 30, 40])
+    plan = serving.geometry_plan(scenes, 500, seed=4)
+    assert len(plan) == 500 and all(p is None for _, p in plan)
+    ks = np.array([k for k, _ in plan])
+    assert set(ks.tolist()) == {0, 1, 2, 3}
+    assert np.array_equal(ks, np.array([k for k, _ in serving.geometry_plan(scenes, 500, seed=4)]))
+
+
+def test_tail_breakdown_separates_queueing_from_size():
+    import bench
+
+    rng = np.random.default_rng(0)
+    n = 3000
+    sps = rng.integers(1, 100, n).astype(np.int64)
+    depth = rng.integers(0, 12, n)
+    # latency made of queueing only: 1 ms per request ahead, size irrelevant
+    lat = (1.0 + depth) * 1e-3
+    rec = {"depth": depth, "late": np.zeros(n)}
+    t = bench.tail_breakdown(lat, sps, rec)
+    assert t["depth_le_2"]["n"] == int(np.sum(depth <= 2)) and t["depth_ge_8"]["n"] == int(np.sum(depth >= 8))
+    assert abs(t["depth_le_2"]["p99_ms"] - 3.0) < 1e-9 and abs(t["depth_ge_8"]["p50_ms"] - 10.0) < 1.0 + 1e-9
+    assert t["p99_tail_behind_8_or_more"] == 1.0
+    assert abs(t["small_third"]["p99_ms"] - t["large_third"]["p99_ms"]) < 1e-9
+    assert abs(t["mean_depth"] - depth.mean()) < 1e-12 and t["max_submit_late_ms"] == 0.0
