@@ -370,24 +370,29 @@ lk_status cuda_fail(lk_ctx* ctx, cudaError_t e, const char* where) {
     } while (0)
 
 // Size class of a pair for tuning: ceil(log2) of its row and column loop sizes.
-uint32_t size_class(int64_t n_rows, int64_t n_cols) {
-    auto clog2 = [](int64_t v) {
-        uint32_t b = 0;
-        while (((int64_t)1 << b) < v) ++b;
-        return b;
-    };
-    return (clog2(n_rows) << 8) | clog2(n_cols);
-}
+// ceil(log2 v) for v >= 1
+inline uint32_t ceil_log2(int64_t v) { return v <= 1 ? 0u : (uint32_t)(64 - __builtin_clzll((uint64_t)(v - 1))); }
 
-int default_tile_rows(int64_t n_rows, int64_t n_cols, int tile_cols, int user_rows) {
+uint32_t size_class(int64_t n_rows, int64_t n_cols) { return (ceil_log2(n_rows) << 8) | ceil_log2(n_cols); }
+
+// Tile widths and the chunk height are powers of two: the packer's ceilings
+// by them are shifts (a list of thousands of pairs is packed per request).
+static_assert((lk::kTileCols & (lk::kTileCols - 1)) == 0 && (lk::kF64TileCols & (lk::kF64TileCols - 1)) == 0 &&
+                  (lk::kChunkRows & (lk::kChunkRows - 1)) == 0,
+              "tile widths and the chunk height must be powers of two");
+inline int64_t ceil_shift(int64_t v, int shift) { return (v + ((int64_t)1 << shift) - 1) >> shift; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return b >= a ? (a > 0 ? 1 : 0) : (a + b - 1) / b; }
+
+int default_tile_rows(int64_t n_rows, int64_t n_cols, int tc_shift, int user_rows) {
     if (user_rows > 0) return user_rows;
-    const int64_t col_tiles = (n_cols + tile_cols - 1) / tile_cols;
-    int64_t row_tiles = (n_rows + 255) / 256;
+    const int64_t col_tiles = ceil_shift(n_cols, tc_shift);
+    int64_t row_tiles = ceil_shift(n_rows, 8);
     const int64_t max_items_per_pair = 1 << 16;
     if (col_tiles * row_tiles > max_items_per_pair)
         row_tiles = std::max<int64_t>(1, max_items_per_pair / col_tiles);
-    int64_t rows = (n_rows + row_tiles - 1) / row_tiles;
-    rows = (rows + lk::kChunkRows - 1) / lk::kChunkRows * lk::kChunkRows;
+    int64_t rows = ceil_div(n_rows, row_tiles);
+    rows = ceil_shift(rows, 5) << 5;                                    // a multiple of kChunkRows
+    static_assert(lk::kChunkRows == 32, "the shift above is by log2 kChunkRows");
     return (int)std::min<int64_t>(rows, INT32_MAX);
 }
 
@@ -400,6 +405,7 @@ int default_tile_rows(int64_t n_rows, int64_t n_cols, int tile_cols, int user_ro
 lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
     const bool f64 = ctx->opt.precision == LK_ALL_F64;
     const int tile_cols = f64 ? lk::kF64TileCols : lk::kTileCols;
+    const int tc_shift = ceil_log2(tile_cols);
     pk.tile_cols = tile_cols;
     pk.tile_rows_max = 0;
     pk.segment_pairs = 0;
@@ -416,8 +422,13 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
         int32_t row_loop, col_loop, n_rows, n_cols, tile_rows, col_tiles, status, accurate;
         int64_t items;
     };
-    std::vector<Shape> sh((size_t)n);
-    std::vector<uint32_t> key((size_t)n);
+    // scratch kept per thread across calls (a server packs a list per
+    // request; fresh vectors would be allocated and faulted in each time)
+    thread_local std::vector<Shape> sh;
+    thread_local std::vector<uint32_t> key;
+    thread_local std::vector<uint64_t> kv, tmp;
+    sh.resize((size_t)n);
+    key.resize((size_t)n);
     const bool tuned = !f64 && ctx->opt.tile_rows <= 0 && !ctx->tune.empty();
     for (int64_t p = 0; p < n; ++p) {
         Shape& t = sh[(size_t)p];
@@ -431,8 +442,8 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
         const int64_t nb = ctx->h_offsets[b + 1] - ctx->h_offsets[b];
         // The orientation that sweeps fewer cells including the padding of the
         // last column tile; on a tie the longer loop is the row loop.
-        const int64_t cells_a_rows = na * ((nb + tile_cols - 1) / tile_cols);
-        const int64_t cells_b_rows = nb * ((na + tile_cols - 1) / tile_cols);
+        const int64_t cells_a_rows = na * ceil_shift(nb, tc_shift);
+        const int64_t cells_b_rows = nb * ceil_shift(na, tc_shift);
         const bool a_rows = cells_a_rows != cells_b_rows ? cells_a_rows < cells_b_rows : na >= nb;
         t.row_loop = a_rows ? a : b;
         t.col_loop = a_rows ? b : a;
@@ -443,9 +454,9 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
             auto it = ctx->tune.find(size_class(t.n_rows, t.n_cols));
             if (it != ctx->tune.end()) rows = it->second;
         }
-        t.tile_rows = default_tile_rows(t.n_rows, t.n_cols, tile_cols, rows);
-        t.col_tiles = (t.n_cols + tile_cols - 1) / tile_cols;
-        t.items = (int64_t)t.col_tiles * ((t.n_rows + t.tile_rows - 1) / t.tile_rows);
+        t.tile_rows = default_tile_rows(t.n_rows, t.n_cols, tc_shift, rows);
+        t.col_tiles = (int32_t)ceil_shift(t.n_cols, tc_shift);
+        t.items = (int64_t)t.col_tiles * ceil_div(t.n_rows, t.tile_rows);
         t.status = LK_OK;
         t.accurate = (int64_t)t.n_rows * t.n_cols >= ctx->opt.accurate_threshold ? 1 : 0;
         const int64_t cost = (int64_t)std::min(t.tile_rows, t.n_rows) * std::min(tile_cols, t.n_cols);
@@ -454,15 +465,23 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
         pk.segment_pairs += (int64_t)t.n_rows * t.n_cols;
         pk.tile_rows_max = std::max(pk.tile_rows_max, t.tile_rows);
     }
-    std::vector<int64_t> order((size_t)n), tmp((size_t)n);
-    std::iota(order.begin(), order.end(), 0);
+    // (key << 32 | index) values, sorted by the key bytes that vary (LSD,
+    // stable: equal keys keep the input order), read and written in sequence
+    kv.resize((size_t)n);
+    tmp.resize((size_t)n);
+    uint32_t varying = 0;
+    const uint32_t key0 = n > 0 ? key[0] : 0u;
+    for (int64_t p = 0; p < n; ++p) {
+        kv[(size_t)p] = ((uint64_t)key[(size_t)p] << 32) | (uint64_t)p;
+        varying |= key[(size_t)p] ^ key0;
+    }
     for (int shift = 0; shift < 32; shift += 8) {
+        if (((varying >> shift) & 0xffu) == 0) continue;                 // one digit value
         size_t cnt[257] = {};
-        for (int64_t k = 0; k < n; ++k) ++cnt[((key[(size_t)order[(size_t)k]] >> shift) & 0xffu) + 1];
-        if (cnt[1 + ((key[(size_t)order[0]] >> shift) & 0xffu)] == (size_t)n) continue;   // one digit value
+        for (int64_t k = 0; k < n; ++k) ++cnt[((kv[(size_t)k] >> (32 + shift)) & 0xffu) + 1];
         for (int d = 0; d < 256; ++d) cnt[d + 1] += cnt[d];
-        for (int64_t k = 0; k < n; ++k) tmp[cnt[(key[(size_t)order[(size_t)k]] >> shift) & 0xffu]++] = order[(size_t)k];
-        order.swap(tmp);
+        for (int64_t k = 0; k < n; ++k) tmp[cnt[(kv[(size_t)k] >> (32 + shift)) & 0xffu]++] = kv[(size_t)k];
+        kv.swap(tmp);
     }
     pk.tasks.resize((size_t)n);
     pk.item_begin.assign((size_t)n + 1, 0);
@@ -471,7 +490,7 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
     pk.n_chunks = 0;
     pk.n_chunk_bits = 0;
     for (int64_t k = 0; k < n; ++k) {
-        const int64_t p = order[(size_t)k];
+        const int64_t p = (int64_t)(kv[(size_t)k] & 0xffffffffu);
         const Shape& q = sh[(size_t)p];
         PairTask t{};
         t.out_index = (int32_t)p;
@@ -493,7 +512,7 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
                 // one bit per chunk slot of each item (the precise sweep skips the
                 // chunks the bulk sweep handed to the careful pass)
                 t.bit_base = pk.n_chunk_bits;
-                pk.n_chunk_bits += q.items * ((q.tile_rows + lk::kChunkRows - 1) / lk::kChunkRows);
+                pk.n_chunk_bits += q.items * ceil_shift(q.tile_rows, 5);
             }
             const bool cc = ctx->opt.method == LK_METHOD_CC;
             const int search = ctx->opt.cc_search;
@@ -518,9 +537,9 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
             } else if (cc) {
                 ++pk.n_cc_sweep;
             }
-            const int64_t full = q.n_rows / q.tile_rows, last = q.n_rows - full * q.tile_rows;
-            const int64_t chunks_per_col = full * ((q.tile_rows + lk::kChunkRows - 1) / lk::kChunkRows) +
-                                           (last > 0 ? (last + lk::kChunkRows - 1) / lk::kChunkRows : 0);
+            const int64_t full = q.tile_rows >= q.n_rows ? (q.tile_rows == q.n_rows ? 1 : 0) : q.n_rows / q.tile_rows;
+            const int64_t last = q.n_rows - full * q.tile_rows;
+            const int64_t chunks_per_col = full * ceil_shift(q.tile_rows, 5) + (last > 0 ? ceil_shift(last, 5) : 0);
             pk.n_chunks += chunks_per_col * q.col_tiles;
         }
         pk.tasks[(size_t)k] = t;
@@ -1753,6 +1772,7 @@ struct lk_server {
     cudaStream_t finish = nullptr;     // each finished request's careful passes, FP64 fix, reduction, copies
     cudaStream_t prep = nullptr;       // geometry requests' search and packing
     Request* stalled = nullptr;        // the first geometry request of this step left waiting for room
+    std::vector<Packed> pk_pool;       // packed tables of admitted requests, reused by later submits
     unsigned char* d_arena = nullptr;
     unsigned char* h_arena = nullptr;
     Arena dev, host;
@@ -2116,6 +2136,10 @@ lk_status admit(lk_server* s) {
         std::memcpy(tb, r->pk.tasks.data(), tbytes);
         std::memcpy(tb + tbytes, r->pk.item_begin.data(), bbytes);
         if (ibytes) std::memcpy(tb + tbytes + bbytes, r->pk.item_task.data(), ibytes);
+        // the tables live on in pinned memory and on the device: their host
+        // vectors go back to the pool (a few, to bound the memory kept)
+        if (s->pk_pool.size() < 8) s->pk_pool.push_back(std::move(r->pk));
+        r->pk = Packed();
         LK_SRV_CUDA(s, cudaMemcpyAsync(r->ws.tasks.p, tb, tbytes, cudaMemcpyHostToDevice, s->stream));
         LK_SRV_CUDA(s, cudaMemcpyAsync(r->ws.item_begin.p, tb + tbytes, bbytes, cudaMemcpyHostToDevice, s->stream));
         if (ibytes)
@@ -2311,6 +2335,10 @@ lk_status lk_server_submit(lk_server* s, lk_ctx* ctx, const int32_t* loop_pairs,
         std::memcpy(r->pairs.data(), loop_pairs, 2 * n_pairs * sizeof(int32_t));
     }
     // A request that could never fit is refused now rather than blocking the queue.
+    if (!s->pk_pool.empty()) {
+        r->pk = std::move(s->pk_pool.back());          // vectors with capacity already
+        s->pk_pool.pop_back();
+    }
     lk_status st = pack_pairs(ctx, r->pairs.data(), n_pairs, r->pk);
     if (st != LK_OK) {
         delete r;
