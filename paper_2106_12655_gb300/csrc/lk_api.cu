@@ -1656,6 +1656,11 @@ size_t request_layout(int64_t n_tasks, int64_t n_items, int64_t n_chunks, bool t
         buf.cap = count;
         off += count * sizeof(T);
     };
+    // Three groups, each contiguous so that one copy or memset serves it:
+    // the uploaded tables (tasks, item_begin, item_task: the layout of the
+    // pinned staging, upload_layout), the buffers that start at zero
+    // (item_fix .. counters), and the results copied back (counters .. status:
+    // the layout of the pinned result block, result_layout).
     if (tables) {
         bind(ws->tasks, P);
         bind(ws->item_begin, P + 1);
@@ -1667,8 +1672,8 @@ size_t request_layout(int64_t n_tasks, int64_t n_items, int64_t n_chunks, bool t
     // list hands items over whole, whose careful re-sum rounds differently,
     // so a result would depend on which items found the list full
     bind(ws->careful_chunks, (size_t)std::max<int64_t>(1, std::min<int64_t>(n_chunks, kServerMaxChunks)));
-    bind(ws->item_fix, I);
     bind(ws->near_list, (size_t)near_cap);
+    bind(ws->item_fix, I);
     bind(ws->fix_acc, P);
     bind(ws->fp64_count, P);
     bind(ws->flags, P);
@@ -1746,9 +1751,35 @@ size_t pack_layout(int64_t T, PackBufs* b, uintptr_t base) {
 constexpr size_t kSumBytes = 64;
 size_t geometry_sum_bytes() { return kSumBytes + (size_t)lk::kTuneClasses * lk::kTuneClasses * sizeof(int32_t); }
 
-size_t request_result_bytes(size_t P) {
-    return ((P * 4 + 255) & ~(size_t)255) + ((P * 8 + 255) & ~(size_t)255) + ((P * 4 + 255) & ~(size_t)255) +
-           256;   // the request's work counters
+inline size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+// Offsets within a request's result group, the same on the device (from
+// ws.counters) and in its pinned result block: counters, lk, raw, status.
+struct ResultLayout {
+    size_t lk, raw, status, copy_bytes;
+};
+ResultLayout result_layout(size_t P) {
+    ResultLayout r;
+    r.lk = 256;                                   // after the 8 counters
+    r.raw = r.lk + align256(P * 4);
+    r.status = r.raw + align256(P * 8);
+    r.copy_bytes = r.status + P * 4;
+    return r;
+}
+
+size_t request_result_bytes(size_t P) { return result_layout(P).status + align256(P * 4); }
+
+// Offsets within the uploaded tables, the same on the device (from
+// ws.tasks) and in the pinned staging: tasks, item_begin, item_task.
+struct UploadLayout {
+    size_t item_begin, item_task, bytes;
+};
+UploadLayout upload_layout(size_t P, size_t I) {
+    UploadLayout u;
+    u.item_begin = align256(P * sizeof(PairTask));
+    u.item_task = u.item_begin + align256((P + 1) * sizeof(int64_t));
+    u.bytes = u.item_task + I * sizeof(int32_t);
+    return u;
 }
 
 // Pinned host bytes of a geometry request's results: lk, raw, status,
@@ -1758,8 +1789,7 @@ size_t geometry_host_bytes(size_t P) { return request_result_bytes(P) + P * 2 * 
 // Pinned host bytes of a request: its results, then its staged item tables.
 size_t request_host_bytes(const Packed& pk) {
     const size_t P = pk.tasks.size();
-    return request_result_bytes(P) + P * sizeof(PairTask) + (P + 1) * sizeof(int64_t) +
-           (size_t)pk.n_items * sizeof(int32_t);
+    return request_result_bytes(P) + upload_layout(P, (size_t)pk.n_items).bytes;
 }
 
 }  // namespace
@@ -1899,12 +1929,20 @@ void complete_now(lk_server* s, Request* r, lk_status error, const std::string& 
 void bind_results(lk_server* s, Request* r) {
     const size_t P = (size_t)r->n_tasks;
     unsigned char* hb = s->h_arena + r->host_off;
-    r->h_lk = reinterpret_cast<int32_t*>(hb);
-    r->h_raw = reinterpret_cast<double*>(hb + ((P * 4 + 255) & ~(size_t)255));
-    r->h_status = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(r->h_raw) + ((P * 8 + 255) & ~(size_t)255));
-    r->h_counters = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(r->h_status) +
-                                                          ((P * 4 + 255) & ~(size_t)255));
+    const ResultLayout L = result_layout(P);
+    r->h_counters = reinterpret_cast<unsigned long long*>(hb);
+    r->h_lk = reinterpret_cast<int32_t*>(hb + L.lk);
+    r->h_raw = reinterpret_cast<double*>(hb + L.raw);
+    r->h_status = reinterpret_cast<int32_t*>(hb + L.status);
     r->h_pairs = reinterpret_cast<int32_t*>(hb + request_result_bytes(P));
+}
+
+// The request's buffers that start at zero (item_fix .. counters, one
+// contiguous range of its work block), cleared with one memset.
+cudaError_t zero_request(const Workspace& ws, cudaStream_t st) {
+    unsigned char* a = reinterpret_cast<unsigned char*>(ws.item_fix.p);
+    unsigned char* b = reinterpret_cast<unsigned char*>(ws.counters.p + 8);
+    return cudaMemsetAsync(a, 0, (size_t)(b - a), st);
 }
 
 // Admission of a geometry request: the potential link search's count pass
@@ -2064,11 +2102,7 @@ lk_status advance_geometry(lk_server* s) {
         r->h_sum = nullptr;
         cudaStream_t st = s->stream;
         lk::launch_pack_item_task(r->ws.item_begin.p, T, r->n_items, r->ws.item_task.p, st);
-        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.counters.p, 0, 8 * sizeof(unsigned long long), st));
-        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.fix_acc.p, 0, T * sizeof(unsigned long long), st));
-        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.fp64_count.p, 0, T * sizeof(unsigned long long), st));
-        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.flags.p, 0, T * sizeof(int), st));
-        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.item_fix.p, 0, r->ws.item_fix.cap * sizeof(unsigned long long), st));
+        LK_SRV_CUDA(s, zero_request(r->ws, st));
         lk::launch_pair_frames(r->ws.tasks.p, T, ctx->d_aabb, st);
         LK_SRV_CUDA(s, cudaGetLastError());
         r->args = request_args(ctx, r->ws, T, r->n_items, s->opt.near_capacity);
@@ -2120,37 +2154,24 @@ lk_status admit(lk_server* s) {
         }
         request_layout(r->pk, s->opt.near_capacity, &r->ws, (uintptr_t)(s->d_arena + r->dev_off));
         const size_t P = (size_t)r->n_tasks;
-        unsigned char* hb = s->h_arena + r->host_off;
-        r->h_lk = reinterpret_cast<int32_t*>(hb);
-        r->h_raw = reinterpret_cast<double*>(hb + ((P * 4 + 255) & ~(size_t)255));
-        r->h_status = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(r->h_raw) + ((P * 8 + 255) & ~(size_t)255));
-        r->h_counters = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(r->h_status) +
-                                                              ((P * 4 + 255) & ~(size_t)255));
+        bind_results(s, r);
         r->args = request_args(ctx, r->ws, r->n_tasks, r->n_items, s->opt.near_capacity);
         // Stage the item tables in pinned memory so that their upload is truly
         // asynchronous (a pageable source would make the copy wait for the
-        // waves already queued on the stream, serialising host and device).
-        unsigned char* tb = hb + request_result_bytes(P);
-        const size_t tbytes = P * sizeof(PairTask), bbytes = (P + 1) * sizeof(int64_t),
-                     ibytes = (size_t)r->pk.n_items * sizeof(int32_t);
-        std::memcpy(tb, r->pk.tasks.data(), tbytes);
-        std::memcpy(tb + tbytes, r->pk.item_begin.data(), bbytes);
-        if (ibytes) std::memcpy(tb + tbytes + bbytes, r->pk.item_task.data(), ibytes);
+        // waves already queued on the stream, serialising host and device),
+        // laid out as on the device so that one copy carries them.
+        unsigned char* tb = s->h_arena + r->host_off + request_result_bytes(P);
+        const UploadLayout U = upload_layout(P, (size_t)r->n_items);
+        std::memcpy(tb, r->pk.tasks.data(), P * sizeof(PairTask));
+        std::memcpy(tb + U.item_begin, r->pk.item_begin.data(), (P + 1) * sizeof(int64_t));
+        if (r->n_items) std::memcpy(tb + U.item_task, r->pk.item_task.data(), (size_t)r->n_items * sizeof(int32_t));
         // the tables live on in pinned memory and on the device: their host
         // vectors go back to the pool (a few, to bound the memory kept)
         if (s->pk_pool.size() < 8) s->pk_pool.push_back(std::move(r->pk));
         r->pk = Packed();
-        LK_SRV_CUDA(s, cudaMemcpyAsync(r->ws.tasks.p, tb, tbytes, cudaMemcpyHostToDevice, s->stream));
-        LK_SRV_CUDA(s, cudaMemcpyAsync(r->ws.item_begin.p, tb + tbytes, bbytes, cudaMemcpyHostToDevice, s->stream));
-        if (ibytes)
-            LK_SRV_CUDA(s, cudaMemcpyAsync(r->ws.item_task.p, tb + tbytes + bbytes, ibytes, cudaMemcpyHostToDevice,
-                                           s->stream));
+        LK_SRV_CUDA(s, cudaMemcpyAsync(r->ws.tasks.p, tb, U.bytes, cudaMemcpyHostToDevice, s->stream));
         const int64_t n = (int64_t)P;
-        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.counters.p, 0, 8 * sizeof(unsigned long long), s->stream));
-        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.fix_acc.p, 0, n * sizeof(unsigned long long), s->stream));
-        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.fp64_count.p, 0, n * sizeof(unsigned long long), s->stream));
-        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.flags.p, 0, n * sizeof(int), s->stream));
-        LK_SRV_CUDA(s, cudaMemsetAsync(r->ws.item_fix.p, 0, r->ws.item_fix.cap * sizeof(unsigned long long), s->stream));
+        LK_SRV_CUDA(s, zero_request(r->ws, s->stream));
         lk::launch_pair_frames(r->ws.tasks.p, n, ctx->d_aabb, s->stream);
         r->state = kRunning;
         r->next_item = 0;
@@ -2245,13 +2266,11 @@ lk_status launch_wave(lk_server* s) {
         ra.status_out = r->ws.status.p;
         lk::launch_reduce(ra, st);
         const size_t P = (size_t)r->n_tasks;
-        LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_lk, r->ws.lk.p, P * 4, cudaMemcpyDeviceToHost, st));
+        // counters, lk, raw and status in one copy (the same layout on both sides)
+        LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_counters, r->ws.counters.p, result_layout(P).copy_bytes,
+                                       cudaMemcpyDeviceToHost, st));
         if (r->geometry)
             LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_pairs, r->d_pairs, P * 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_raw, r->ws.raw.p, P * 8, cudaMemcpyDeviceToHost, st));
-        LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_status, r->ws.status.p, P * 4, cudaMemcpyDeviceToHost, st));
-        LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_counters, r->ws.counters.p, 8 * sizeof(unsigned long long),
-                                       cudaMemcpyDeviceToHost, st));
     }
     LK_SRV_CUDA(s, cudaGetLastError());
     LK_SRV_CUDA(s, cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming));
