@@ -203,6 +203,7 @@ def serving_block(args):
                                  "tail": tail_breakdown(lat, sps, rec)})
         out["server_stats"] = lk.lk_server_get_stats(srv)
         out["potential_link_search"] = pls_block(scenes)
+        out["potential_link_search_large"] = pls_large_block()
         out["batched_same_piles"] = batched_piles_block(scenes)
         return out
     finally:
@@ -324,6 +325,36 @@ def pls_block(scenes):
                     "box_tests_per_s": sc.geometry.n_loops * (sc.geometry.n_loops - 1) / 2 / statistics.median(ts[2:]),
                     "equals_pile_pairs": bool(got.shape == want.shape and np.array_equal(got, want))})
     return out
+
+
+def pls_large_block(rows=250, cols=400, nseg=32):
+    """The device potential link search on a 100,000-ring chainmail pile
+    (sort and sweep: above 2^27 box pairs): wall time of the synchronous call
+    into a device buffer (median of 10 after 2), and whether its list equals
+    the pile's candidate list from the host's sort and sweep."""
+    import torch
+    from paper_2106_12655_gb300 import lk
+    from paper_2106_12655_gb300 import workloads as W
+
+    g = W.chainmail(seed=31, rows=rows, cols=cols, nseg=nseg)
+    ctx = lk.lk_create(g.vertices, g.offsets)
+    try:
+        n = lk.lk_candidates(ctx, np.zeros((0, 2), np.int32))
+        buf = torch.zeros((max(n, 1), 2), dtype=torch.int32, device="cuda")
+        ts = []
+        for _ in range(12):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lk.lk_candidates(ctx, buf)
+            ts.append(time.perf_counter() - t0)
+        got = buf[:n].cpu().numpy()
+    finally:
+        lk.lk_destroy(ctx)
+    want = np.ascontiguousarray(g.pairs)
+    ms = 1e3 * statistics.median(ts[2:])
+    return {"rings": g.n_loops, "segments_per_ring": nseg, "candidates": n, "ms": ms,
+            "box_pairs": g.n_loops * (g.n_loops - 1) // 2,
+            "equals_pile_pairs": bool(got.shape == want.shape and np.array_equal(got, want))}
 
 
 def counting_crossings_block(g, v, off, pairs_d, lk_ref, stream, flush, steps=20, search=None):
@@ -1065,6 +1096,7 @@ def summary(line):
         sv = line["serving"]
         out["serving"] = {"cap_req_s": _g(sv["capacity"]["req_per_s"]), "cap_sp_s": _g(sv["capacity"]["sp_per_s"]),
                           "batched_sp_s": _g(sv["batched_same_piles"]["sp_per_s"]),
+                          "pls_100k_ms": _g(sv["potential_link_search_large"]["ms"]),
                           "n_req": sv["loads"][0]["n_requests"],
                           "p50_ms": [_g(x["p50_ms"]) for x in sv["loads"]],
                           "p99_ms": [_g(x["p99_ms"]) for x in sv["loads"]]}
