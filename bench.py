@@ -579,8 +579,9 @@ def stress_block(stream):
 
 def configs_block(stream, reps=3, oracle_threads=None):
     """The other workloads of the benchmark's configurations, each verified
-    through lk_verify (CUDA-event medians of `reps` verifies after untimed
-    ones) and, where the FP64 oracle can run in seconds, checked against it
+    through lk_verify with the pair list in pinned host memory and the results
+    on the device (CUDA-event medians of `reps` verifies after untimed ones)
+    and, where the FP64 oracle can run in seconds, checked against it
     result by result (max, p99 and argmax of |raw - oracle|):
       * ring chain: 16 rings x 128 segments, FP64 vertices, all 120 pairs
         (latency-bound; the oracle runs on every pair);
@@ -611,7 +612,9 @@ def configs_block(stream, reps=3, oracle_threads=None):
             setattr(o, k, val)
         ctx = lk.lk_create(v, off, o, stream)
         try:
-            pd = torch.from_numpy(np.ascontiguousarray(pairs)).cuda()
+            # the list in pinned host memory, where a caller keeps it (a device
+            # list is read back to the host, with a synchronisation, each call)
+            pd = torch.from_numpy(np.ascontiguousarray(pairs)).pin_memory()
             ms, lo, raw, st, est = timed_verify(ctx, pd, pairs.shape[0], stream, warm, reps_, v.device)
             stats = lk.lk_get_stats(ctx)
         finally:
