@@ -206,3 +206,44 @@ def test_no_candidates_small_buffer_and_arena_limits():
     finally:
         lk.lk_server_destroy(srv)
         lk.lk_destroy(ctx)
+
+
+def test_mixed_geometry_and_list_requests_equal_their_solo_results():
+    gs = [W.serving_pile(110 + k, 150, 600) for k in range(3)]
+    ctxs = [lk.lk_create(g.vertices, g.offsets) for g in gs]
+    o = lk.lk_server_default_options()
+    o.wave_items = 1024                      # several requests share each wave
+    try:
+        # each request alone on a fresh server
+        solo = {}
+        for k, c in enumerate(ctxs):
+            srv = lk.lk_server_create(o)
+            try:
+                t = lk.lk_server_submit_geometry(srv, c)
+                solo[("g", k)] = take_all(srv, [t])[t]
+                half = np.ascontiguousarray(gs[k].pairs[::2])
+                t = lk.lk_server_submit(srv, c, half)
+                solo[("l", k)] = take_all(srv, [t])[t]
+            finally:
+                lk.lk_server_destroy(srv)
+        # all of them interleaved, twice over, on one server
+        srv = lk.lk_server_create(o)
+        try:
+            which = {}
+            for rep in range(2):
+                for k, c in enumerate(ctxs):
+                    which[lk.lk_server_submit_geometry(srv, c)] = ("g", k)
+                    which[lk.lk_server_submit(srv, c, np.ascontiguousarray(gs[k].pairs[::2]))] = ("l", k)
+                    lk.lk_server_step(srv)
+            res = take_all(srv, list(which))
+            assert lk.lk_server_get_stats(srv)["max_requests_per_wave"] >= 2
+        finally:
+            lk.lk_server_destroy(srv)
+        for t, key in which.items():
+            for a, b in zip(res[t], solo[key]):
+                assert np.array_equal(a, b)
+        for k, g in enumerate(gs):
+            check_against_oracle(g, solo[("g", k)], n_sample=100, seed=k)
+    finally:
+        for c in ctxs:
+            lk.lk_destroy(c)
