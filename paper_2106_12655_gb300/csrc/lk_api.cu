@@ -427,6 +427,17 @@ lk_status pack_pairs(lk_ctx* ctx, const int32_t* pairs, int64_t n, Packed& pk) {
     thread_local std::vector<Shape> sh;
     thread_local std::vector<uint32_t> key;
     thread_local std::vector<uint64_t> kv, tmp;
+    // ... but not after a list of millions of pairs (68 B a pair)
+    struct Release {
+        int64_t n;
+        ~Release() {
+            if (n <= ((int64_t)1 << 20)) return;
+            std::vector<Shape>().swap(sh);
+            std::vector<uint32_t>().swap(key);
+            std::vector<uint64_t>().swap(kv);
+            std::vector<uint64_t>().swap(tmp);
+        }
+    } release{n};
     sh.resize((size_t)n);
     key.resize((size_t)n);
     const bool tuned = !f64 && ctx->opt.tile_rows <= 0 && !ctx->tune.empty();
@@ -2166,8 +2177,10 @@ lk_status admit(lk_server* s) {
         std::memcpy(tb + U.item_begin, r->pk.item_begin.data(), (P + 1) * sizeof(int64_t));
         if (r->n_items) std::memcpy(tb + U.item_task, r->pk.item_task.data(), (size_t)r->n_items * sizeof(int32_t));
         // the tables live on in pinned memory and on the device: their host
-        // vectors go back to the pool (a few, to bound the memory kept)
-        if (s->pk_pool.size() < 8) s->pk_pool.push_back(std::move(r->pk));
+        // vectors go back to the pool (a few, of at most 2^20 pairs, to bound
+        // the memory kept)
+        if (s->pk_pool.size() < 8 && r->pk.tasks.capacity() <= ((size_t)1 << 20))
+            s->pk_pool.push_back(std::move(r->pk));
         r->pk = Packed();
         LK_SRV_CUDA(s, cudaMemcpyAsync(r->ws.tasks.p, tb, U.bytes, cudaMemcpyHostToDevice, s->stream));
         const int64_t n = (int64_t)P;
