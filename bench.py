@@ -169,8 +169,10 @@ class ClockSampler:
 
 def serving_block(args):
     """Open-loop Poisson serving over resident chainmail piles (500-14,000 rings,
-    64-256 segments per ring, 1k-20k pairs per request): capacity, then p50/p99
-    latency at 50/80/95% of it."""
+    64-256 segments per ring, 1k-20k pairs per request) with the default
+    server (lists packed on the device): capacity, then p50/p99 latency at
+    50/80/95% of it; then the same at 80% with host packing and with the
+    fewest-items-first wave order."""
     from paper_2106_12655_gb300 import lk
     from paper_2106_12655_gb300 import serving as S
 
@@ -202,6 +204,8 @@ def serving_block(args):
                                  "n_requests": len(plan), "nonok_pair_status": bad,
                                  "tail": tail_breakdown(lat, sps, rec)})
         out["server_stats"] = lk.lk_server_get_stats(srv)
+        out["host_packing"] = server_variant_block(args, scenes, cap, pack_on_device=0)
+        out["fewest_items_first"] = server_variant_block(args, scenes, cap, wave_order=1)
         out["potential_link_search"] = pls_block(scenes)
         out["potential_link_search_large"] = pls_large_block()
         out["batched_same_piles"] = batched_piles_block(scenes)
@@ -209,6 +213,33 @@ def serving_block(args):
     finally:
         lk.lk_server_destroy(srv)
         S.close(scenes)
+
+
+def server_variant_block(args, scenes, cap, load=0.8, **options):
+    """A server with other options on the same piles: its closed-loop capacity
+    (32 outstanding), then the 80%-load plan at the default server's offered
+    rate (0.8 x `cap`), with the tail breakdown."""
+    from paper_2106_12655_gb300 import lk
+    from paper_2106_12655_gb300 import serving as S
+
+    o = lk.lk_server_default_options()
+    for k, v in options.items():
+        setattr(o, k, v)
+    srv = lk.lk_server_create(o)
+    try:
+        S.run(srv, scenes, S.request_plan(scenes, 40, seed=99), None, max_outstanding=32)
+        cap_plan = S.request_plan(scenes, max(100, args.serving_requests // 2), seed=1)
+        _, wall, bad_cap, _ = S.run(srv, scenes, cap_plan, None, max_outstanding=32)
+        plan = S.request_plan(scenes, args.serving_requests, seed=int(load * 100))
+        rec = {}
+        lat, wall2, bad, _ = S.run(srv, scenes, plan, rate_per_s=load * cap, seed=int(load * 1000), record=rec)
+        pairs, sps = S.plan_sizes(scenes, plan)
+        return {"options": options, "capacity_req_per_s": len(cap_plan) / wall, "load": load,
+                "offered_req_per_s": load * cap, "req_per_s": len(plan) / wall2,
+                "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "n_requests": len(plan), "nonok_pair_status": bad + bad_cap, "tail": tail_breakdown(lat, sps, rec)}
+    finally:
+        lk.lk_server_destroy(srv)
 
 
 def tail_breakdown(lat, sps, rec):
@@ -1102,7 +1133,10 @@ def summary(line):
                           "pls_100k_ms": _g(sv["potential_link_search_large"]["ms"]),
                           "n_req": sv["loads"][0]["n_requests"],
                           "p50_ms": [_g(x["p50_ms"]) for x in sv["loads"]],
-                          "p99_ms": [_g(x["p99_ms"]) for x in sv["loads"]]}
+                          "p99_ms": [_g(x["p99_ms"]) for x in sv["loads"]],
+                          "variants_cap_p50_p99_80": {k: [_g(sv[k]["capacity_req_per_s"]), _g(sv[k]["p50_ms"]),
+                                                          _g(sv[k]["p99_ms"])]
+                                                      for k in ("host_packing", "fewest_items_first")}}
     if "serving_geometry" in line:
         sg = line["serving_geometry"]
         out["serving_geometry"] = {m: {"cap_req_s": _g(sg[m]["capacity"]["req_per_s"]),

@@ -373,6 +373,15 @@ typedef struct lk_server_options {
                              has ~1.5 near segment pairs per loop pair, and entries beyond
                              the list are evaluated in place, much more slowly) */
     int max_queue;        /* queued requests before submit returns LK_ERR_BUSY (default 65536) */
+    int wave_order;       /* which admitted requests' items a wave takes first: 0 (default) in
+                             admission order, 1 the requests with the fewest items left first
+                             (shortest remaining work; a result never depends on the order) */
+    int pack_on_device;   /* 1 (default): a pair-list request's list is uploaded as it is and laid
+                             out as work items on the device (the packing geometry-only requests
+                             use), so submit does not pack on the host; its work buffers are then
+                             sized only once the packing is done, and a request whose work does
+                             not fit the arena fails when polled (LK_ERR_OOM).  0: host packing
+                             at submit, where a request too large for the arena is refused */
 } lk_server_options;
 
 typedef struct lk_server_stats {
@@ -397,7 +406,8 @@ lk_status lk_server_create(lk_server** out, const lk_server_options* opt);
 void* lk_server_stream(lk_server* srv);
 /* Queue a request to verify n_pairs >= 1 pairs of ctx (host or device memory,
  * copied).  *ticket identifies it.  Errors: LK_ERR_ARG; LK_ERR_BUSY (queue
- * full); LK_ERR_OOM (the request alone exceeds the arena). */
+ * full); LK_ERR_OOM (the request alone exceeds the arena: with pack_on_device
+ * its list and tables, the work buffers failing at poll instead). */
 lk_status lk_server_submit(lk_server* srv, lk_ctx* ctx, const int32_t* loop_pairs, int64_t n_pairs,
                            int64_t* ticket);
 /* Queue a request that carries geometry only: verify every potential link of

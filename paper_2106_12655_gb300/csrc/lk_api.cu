@@ -1624,6 +1624,7 @@ struct Request {
     // Geometry requests: the pairs are the potential link search's candidates
     // of the context, found and packed on the device (lk_server_submit_geometry).
     bool geometry = false;
+    bool dev_pack = false;               // a pair list packed on the device (pack_on_device)
     bool sweep = false;                  // sort-and-sweep search (else every box pair)
     bool tuned = false;                  // the context's tune table goes to the packer
     lk_status error = LK_OK;             // set when the request could not run
@@ -1762,6 +1763,16 @@ size_t pack_layout(int64_t T, PackBufs* b, uintptr_t base) {
 constexpr size_t kSumBytes = 64;
 size_t geometry_sum_bytes() { return kSumBytes + (size_t)lk::kTuneClasses * lk::kTuneClasses * sizeof(int32_t); }
 
+// A pair-list request packed on the device: its pack block (the pack layout,
+// then the tune table) and its pinned block (results, the staged list, the
+// totals read back and the tune table).
+size_t devpack_dev_bytes(int64_t T) {
+    PackBufs pb;
+    return ((pack_layout(T, &pb, 0) + 255) & ~(size_t)255) +
+           (size_t)lk::kTuneClasses * lk::kTuneClasses * sizeof(int32_t);
+}
+size_t devpack_host_bytes(int64_t T);
+
 inline size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 // Offsets within a request's result group, the same on the device (from
@@ -1796,6 +1807,10 @@ UploadLayout upload_layout(size_t P, size_t I) {
 // Pinned host bytes of a geometry request's results: lk, raw, status,
 // counters, then its pair list.
 size_t geometry_host_bytes(size_t P) { return request_result_bytes(P) + P * 2 * sizeof(int32_t); }
+
+size_t devpack_host_bytes(int64_t T) {
+    return request_result_bytes((size_t)T) + align256((size_t)T * 2 * sizeof(int32_t)) + geometry_sum_bytes();
+}
 
 // Pinned host bytes of a request: its results, then its staged item tables.
 size_t request_host_bytes(const Packed& pk) {
@@ -2012,6 +2027,67 @@ bool start_search(lk_server* s, Request* r, lk_status* err) {
     return true;
 }
 
+// Admission of a pair-list request packed on the device: its list staged in
+// pinned memory and uploaded, then the device packer (as for a geometry
+// request's candidates) on the preparation stream; the totals are read back
+// without waiting.  Returns false when the arenas have no room yet.
+bool start_devpack(lk_server* s, Request* r, lk_status* err) {
+    lk_ctx* ctx = r->ctx;
+    const int64_t T = r->n_tasks;
+    *err = LK_OK;
+    const size_t blk = devpack_dev_bytes(T), hbytes = devpack_host_bytes(T);
+    if (!s->dev.alloc(blk, &r->blk_off)) return false;
+    if (!s->host.alloc(hbytes, &r->host_off)) {
+        s->dev.release(r->blk_off, blk);
+        return false;
+    }
+    r->blk_bytes = blk;
+    r->host_bytes = hbytes;
+    bind_results(s, r);                               // h_pairs: the staged list
+    unsigned char* hb = s->h_arena + r->host_off;
+    r->h_sum = reinterpret_cast<long long*>(hb + request_result_bytes((size_t)T) +
+                                            align256((size_t)T * 2 * sizeof(int32_t)));
+    std::memcpy(r->h_pairs, r->pairs.data(), (size_t)T * 2 * sizeof(int32_t));
+    PackBufs pb;
+    const size_t off = pack_layout(T, &pb, (uintptr_t)(s->d_arena + r->blk_off));
+    int32_t* d_tune = reinterpret_cast<int32_t*>(s->d_arena + r->blk_off + align256(off));
+    cudaStream_t st = s->prep;
+    auto check = [&](cudaError_t e) {
+        if (e != cudaSuccess && *err == LK_OK) {
+            *err = LK_ERR_CUDA;
+            s->err = std::string("lk_server_step (device packing): ") + cudaGetErrorString(e);
+        }
+    };
+    if (!r->ev) check(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
+    check(cudaMemcpyAsync(pb.pairs, r->h_pairs, (size_t)T * 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (r->tuned) {
+        int32_t* h_tune = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(r->h_sum) + kSumBytes);
+        std::fill(h_tune, h_tune + lk::kTuneClasses * lk::kTuneClasses, 0);
+        for (const auto& kv : ctx->tune) {
+            const uint32_t rc = kv.first >> 8, cc = kv.first & 0xffu;
+            if (rc < (uint32_t)lk::kTuneClasses && cc < (uint32_t)lk::kTuneClasses)
+                h_tune[rc * lk::kTuneClasses + cc] = kv.second;
+        }
+        check(cudaMemcpyAsync(d_tune, h_tune, (size_t)lk::kTuneClasses * lk::kTuneClasses * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, st));
+    }
+    const lk::PackParams P{ctx->d_V, ctx->d_R, ctx->d_offsets, r->tuned ? d_tune : nullptr,
+                           ctx->opt.accurate_threshold, ctx->opt.tile_rows, (int32_t)ctx->n_loops};
+    const unsigned npk = lk::pls_sort_size(T);
+    lk::launch_pack_keys(pb.pairs, T, P, pb.keys, npk, st);
+    lk::launch_bitonic_sort(pb.keys, npk, st);
+    lk::launch_pack_tasks(pb.keys, pb.pairs, T, P, pb.tasks, pb.sums, pb.scan, pb.scratch, pb.item_begin, st);
+    check(cudaMemcpyAsync(r->h_sum + 1, pb.scan + T, sizeof(lk::PackSums), cudaMemcpyDeviceToHost, st));
+    check(cudaGetLastError());
+    check(cudaEventRecord(r->ev, st));
+    r->d_pairs = pb.pairs;
+    r->ws.tasks.p = pb.tasks;
+    r->ws.tasks.cap = (size_t)T;
+    r->ws.item_begin.p = pb.item_begin;
+    r->ws.item_begin.cap = (size_t)T + 1;
+    return true;
+}
+
 // Advance geometry requests whose search or packing has finished on the
 // device (polled, never waited for).
 lk_status advance_geometry(lk_server* s) {
@@ -2058,7 +2134,7 @@ lk_status advance_geometry(lk_server* s) {
             SearchBufs sb;
             search_layout(L, r->sweep, &sb, (uintptr_t)(s->d_arena + r->scr_off));
             const lk::PackParams P{ctx->d_V, ctx->d_R, ctx->d_offsets, r->tuned ? sb.tune : nullptr,
-                                   ctx->opt.accurate_threshold, ctx->opt.tile_rows, 0};
+                                   ctx->opt.accurate_threshold, ctx->opt.tile_rows, (int32_t)ctx->n_loops};
             cudaStream_t st = s->prep;
             const unsigned npk = lk::pls_sort_size(T);
             if (r->sweep) {
@@ -2107,8 +2183,8 @@ lk_status advance_geometry(lk_server* s) {
         r->n_chunks = tot.chunks;
         request_layout(T, r->n_items, r->n_chunks, false, s->opt.near_capacity, &r->ws,
                        (uintptr_t)(s->d_arena + r->dev_off));
-        s->dev.release(r->scr_off, r->scr_bytes);
-        s->host.release(r->sum_off, r->sum_bytes);
+        if (r->scr_bytes) s->dev.release(r->scr_off, r->scr_bytes);
+        if (r->sum_bytes) s->host.release(r->sum_off, r->sum_bytes);
         r->scr_bytes = r->sum_bytes = 0;
         r->h_sum = nullptr;
         cudaStream_t st = s->stream;
@@ -2119,7 +2195,7 @@ lk_status advance_geometry(lk_server* s) {
         r->args = request_args(ctx, r->ws, T, r->n_items, s->opt.near_capacity);
         r->state = kRunning;
         r->next_item = 0;
-        s->st.candidate_pairs += T;
+        if (r->geometry) s->st.candidate_pairs += T;
     }
     return LK_OK;
 }
@@ -2129,6 +2205,16 @@ lk_status admit(lk_server* s) {
     while (!s->queue.empty() && (int)s->running.size() < s->opt.max_requests) {
         Request* r = s->queue.front();
         lk_ctx* ctx = r->ctx;
+        if (r->dev_pack) {
+            lk_status err = LK_OK;
+            if (!start_devpack(s, r, &err)) break;      // no room yet
+            if (err != LK_OK) return err;
+            r->state = kPacking;
+            s->running.push_back(r);
+            s->queue.pop_front();
+            s->st.admitted += 1;
+            continue;
+        }
         if (r->geometry) {
             s->running.push_back(r);
             s->queue.pop_front();
@@ -2212,8 +2298,16 @@ lk_status launch_wave(lk_server* s) {
     int64_t budget = s->opt.wave_items;
     std::vector<Request*> completing;
     int64_t touched = 0;
-    for (Request* r : s->running) {
-        if (r->state != kRunning || budget <= 0 || n_acc + n_fast + 2 > kMaxSegs) continue;
+    std::vector<Request*> order;
+    order.reserve(s->running.size());
+    for (Request* r : s->running)
+        if (r->state == kRunning) order.push_back(r);
+    if (s->opt.wave_order == 1)        // fewest items left first; ties in admission order
+        std::stable_sort(order.begin(), order.end(), [](const Request* a, const Request* b) {
+            return a->n_items - a->next_item < b->n_items - b->next_item;
+        });
+    for (Request* r : order) {
+        if (budget <= 0 || n_acc + n_fast + 2 > kMaxSegs) continue;
         ++touched;
         const int64_t lo = r->next_item, hi = std::min<int64_t>(r->n_items, lo + budget);
         // accurate items are [0, n_acc_items), fast items after them
@@ -2308,6 +2402,8 @@ void lk_server_default_options(lk_server_options* o) {
     o->wave_items = 16384;
     o->near_capacity = 1 << 16;
     o->max_queue = 1 << 16;
+    o->wave_order = 0;
+    o->pack_on_device = 1;
 }
 
 lk_status lk_server_create(lk_server** out, const lk_server_options* opt) {
@@ -2317,7 +2413,8 @@ lk_status lk_server_create(lk_server** out, const lk_server_options* opt) {
     lk_server_default_options(&o);
     if (opt) o = *opt;
     if (o.max_requests < 1 || o.wave_items < 1 || o.near_capacity < 1 || o.arena_bytes < 4096 ||
-        o.host_bytes < 4096 || o.max_queue < 1)
+        o.host_bytes < 4096 || o.max_queue < 1 || o.wave_order < 0 || o.wave_order > 1 ||
+        o.pack_on_device < 0 || o.pack_on_device > 1)
         return srv_fail(nullptr, LK_ERR_ARG, "lk_server_create: invalid options");
     lk_server* s = new lk_server();
     s->opt = o;
@@ -2365,6 +2462,25 @@ lk_status lk_server_submit(lk_server* s, lk_ctx* ctx, const int32_t* loop_pairs,
         }
     } else {
         std::memcpy(r->pairs.data(), loop_pairs, 2 * n_pairs * sizeof(int32_t));
+    }
+    if (s->opt.pack_on_device) {
+        // the list is packed on the device at admission; only its pack block
+        // and pinned block can be checked against the arenas now
+        r->dev_pack = true;
+        r->packed = true;
+        r->n_tasks = n_pairs;
+        r->tuned = ctx->opt.tile_rows <= 0 && !ctx->tune.empty();
+        if (Arena::round(devpack_dev_bytes(n_pairs)) > s->opt.arena_bytes ||
+            Arena::round(devpack_host_bytes(n_pairs)) > s->opt.host_bytes) {
+            delete r;
+            return srv_fail(s, LK_ERR_OOM, "lk_server_submit: request larger than the server's arena");
+        }
+        r->ticket = s->next_ticket++;
+        s->queue.push_back(r);
+        s->all[r->ticket] = r;
+        s->st.submitted += 1;
+        *ticket = r->ticket;
+        return LK_OK;
     }
     // A request that could never fit is refused now rather than blocking the queue.
     if (!s->pk_pool.empty()) {

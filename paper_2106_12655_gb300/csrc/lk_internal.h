@@ -281,7 +281,7 @@ struct PackParams {
     const int32_t* tune;           // [kTuneClasses^2] tile rows per (row, column) size class, 0 = none; or null
     int64_t accurate_threshold;    // segment pairs from which a pair takes the accurate variant
     int32_t user_rows;             // fixed tile rows (> 0), else the tune table or the default
-    int32_t pad;
+    int32_t n_loops;               // pairs outside [0, n_loops) or of one loop get status LK_ERR_ARG
 };
 struct PackSums {
     long long items, chunks, acc_items, segment_pairs;

@@ -1,7 +1,7 @@
-// Device-side work packing for requests that carry geometry only: the pairs
-// come from the potential link search (Sec. 3.2, Algorithm 2) on the device,
-// and are laid out as work items on the device, so that no pair list passes
-// through the host.
+// Device-side work packing of a pair list that lives on the device: the
+// candidates of a geometry-only serving request (the potential link search,
+// Sec. 3.2, Algorithm 2, run on the device), or a served pair list uploaded
+// as it is, laid out as work items without the host packer.
 //
 // The layout is the one the host packer gives the same list (a pair's tiling
 // depends only on its two loop sizes and the tune table; accurate-variant
@@ -19,6 +19,7 @@
 // sums, in a fixed order.
 #include <algorithm>
 
+#include "lk.h"
 #include "lk_internal.h"
 
 namespace lk {
@@ -134,7 +135,7 @@ void scan(const In* in, int64_t n, T* out, T* scratch, cudaStream_t s) {
 }
 
 struct Shape {
-    int32_t row_loop, col_loop, n_rows, n_cols, tile_rows, col_tiles, accurate;
+    int32_t row_loop, col_loop, n_rows, n_cols, tile_rows, col_tiles, accurate, status;
     int64_t items, chunks;
     uint32_t key;
 };
@@ -147,7 +148,13 @@ __device__ __forceinline__ uint32_t ceil_log2(int64_t v) {
 
 // The shape of pair (a, b), as the host packer computes it.
 __device__ Shape pair_shape(const PackParams& P, int32_t a, int32_t b) {
-    Shape t;
+    Shape t{};
+    if (a < 0 || b < 0 || a >= P.n_loops || b >= P.n_loops || a == b) {
+        t.status = LK_ERR_ARG;              // no items; sorted after every valid pair
+        t.key = 0xffffffffu;
+        return t;
+    }
+    t.status = LK_OK;
     const int64_t tc = kTileCols;
     const int64_t na = P.offsets[a + 1] - P.offsets[a];
     const int64_t nb = P.offsets[b + 1] - P.offsets[b];
@@ -209,6 +216,14 @@ __global__ void pack_tasks_kernel(const unsigned long long* __restrict__ keys, c
     const int32_t p = (int32_t)(keys[k] & 0xffffffffu);
     const Shape t = pair_shape(P, pairs[2 * p], pairs[2 * p + 1]);
     PairTask q{};
+    if (t.status != LK_OK) {
+        q.out_index = p;
+        q.status = t.status;
+        q.scale = 1.0f;
+        tasks[k] = q;
+        sums[k] = PackSums{0, 0, 0, 0};
+        return;
+    }
     q.V = P.V;
     q.R = P.R;
     q.row_loop = t.row_loop;

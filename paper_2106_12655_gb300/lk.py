@@ -68,7 +68,8 @@ class lk_stats(ctypes.Structure):
 class lk_server_options(ctypes.Structure):
     _fields_ = [("max_requests", ctypes.c_int), ("arena_bytes", ctypes.c_size_t),
                 ("host_bytes", ctypes.c_size_t), ("wave_items", ctypes.c_int64),
-                ("near_capacity", ctypes.c_int), ("max_queue", ctypes.c_int)]
+                ("near_capacity", ctypes.c_int), ("max_queue", ctypes.c_int), ("wave_order", ctypes.c_int),
+                ("pack_on_device", ctypes.c_int)]
 
 
 class lk_server_stats(ctypes.Structure):

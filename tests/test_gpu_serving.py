@@ -100,7 +100,10 @@ def test_admission_waits_for_arena_memory():
     ctx = lk.lk_create(g.vertices, g.offsets)
     # measure one request's arena footprint, then give the server room for
     # one such request at a time
-    probe = lk.lk_server_create(None)
+    # (host packing: a request's whole footprint is known when it is submitted)
+    o0 = lk.lk_server_default_options()
+    o0.pack_on_device = 0
+    probe = lk.lk_server_create(o0)
     t = lk.lk_server_submit(probe, ctx, g.pairs)
     lk.lk_server_step(probe)
     one = lk.lk_server_get_stats(probe)["arena_used"]
@@ -108,6 +111,7 @@ def test_admission_waits_for_arena_memory():
     lk.lk_server_destroy(probe)
     assert one > 0
     o = lk.lk_server_default_options()
+    o.pack_on_device = 0
     o.arena_bytes = int(one * 1.5)
     o.wave_items = 256
     srv = lk.lk_server_create(o)
@@ -213,3 +217,141 @@ def test_fp64_list_overflow_is_reported_and_exact():
     finally:
         lk.lk_server_destroy(srv)
         lk.lk_destroy(ctx)
+
+
+def test_fewest_items_first_order_changes_no_result():
+    gs = scenes()
+    ctxs = [lk.lk_create(g.vertices, g.offsets) for g in gs]
+    o = lk.lk_server_default_options()
+    o.wave_items = 512
+    o.wave_order = 1
+    srv = lk.lk_server_create(o)
+    try:
+        tickets, sizes, which = [], {}, {}
+        for rep in range(2):
+            for k, (g, ctx) in enumerate(zip(gs, ctxs)):
+                pairs = np.ascontiguousarray(g.pairs if rep == 0 else g.pairs[: max(1, g.pairs.shape[0] // 3)])
+                t = lk.lk_server_submit(srv, ctx, pairs)
+                tickets.append(t)
+                sizes[t] = pairs.shape[0]
+                which[t] = (k, pairs)
+        res = drain(srv, tickets, sizes)
+        assert lk.lk_server_get_stats(srv)["max_requests_per_wave"] >= 2
+        for t in tickets:
+            k, pairs = which[t]
+            ref = alone(ctxs[k], pairs)
+            for a, b in zip(res[t], ref):
+                assert np.array_equal(a, b)
+    finally:
+        lk.lk_server_destroy(srv)
+        for c in ctxs:
+            lk.lk_destroy(c)
+    bad = lk.lk_server_default_options()
+    bad.wave_order = 2
+    with pytest.raises(lk.LkError):
+        lk.lk_server_create(bad)
+
+
+def test_lists_packed_on_the_device_equal_host_packing():
+    gs = scenes()
+    ctxs = [lk.lk_create(g.vertices, g.offsets) for g in gs]
+    # a tune table on one context reaches the device packer too
+    lk.lk_tune_set(ctxs[1], np.array([[r, c, 64] for r in range(6, 9) for c in range(6, 9)], np.int32))
+    lists = []
+    rng = np.random.default_rng(3)
+    for k, g in enumerate(gs):
+        p = np.ascontiguousarray(g.pairs[rng.permutation(g.pairs.shape[0])])
+        if k == 0:       # invalid pairs: a loop with itself, an index past the end, a negative one
+            bad = np.array([[0, 0], [1, g.n_loops], [-1, 2]], np.int32)
+            p = np.ascontiguousarray(np.concatenate([p[:5], bad, p[5:]]))
+        lists.append((k, p))
+    results = []
+    for on_device in (0, 1):
+        o = lk.lk_server_default_options()
+        o.wave_items = 512
+        o.pack_on_device = on_device
+        srv = lk.lk_server_create(o)
+        try:
+            tickets, sizes = [], {}
+            for k, p in lists:
+                t = lk.lk_server_submit(srv, ctxs[k], p)
+                tickets.append(t)
+                sizes[t] = p.shape[0]
+            res = drain(srv, tickets, sizes)
+            results.append([res[t] for t in tickets])
+        finally:
+            lk.lk_server_destroy(srv)
+    for a, b in zip(*results):
+        for x, y in zip(a, b):
+            # invalid pairs have no raw sum (NaN) on both servers
+            assert np.array_equal(x, y, equal_nan=bool(np.issubdtype(x.dtype, np.floating)))
+    st0 = results[1][0][2]
+    assert (st0[5:8] == lk.LK_ERR_ARG).all() and (np.delete(st0, [5, 6, 7]) == 0).all()
+    # a list of invalid pairs only
+    o = lk.lk_server_default_options()
+    o.pack_on_device = 1
+    srv = lk.lk_server_create(o)
+    try:
+        bad = np.array([[0, 0], [3, 3]], np.int32)
+        t = lk.lk_server_submit(srv, ctxs[0], bad)
+        res = drain(srv, [t], {t: 2})[t]
+        assert (res[2] == lk.LK_ERR_ARG).all()
+    finally:
+        lk.lk_server_destroy(srv)
+        for c in ctxs:
+            lk.lk_destroy(c)
+    o.pack_on_device = 2
+    with pytest.raises(lk.LkError):
+        lk.lk_server_create(o)
+
+
+def test_device_packed_requests_wait_for_room_and_fail_at_poll_when_too_large():
+    g = W.chainmail(seed=7, rows=8, cols=16)
+    ctx = lk.lk_create(g.vertices, g.offsets)
+    torus = W.torus_link(2, 3, 100_000, dtype=np.float32)
+    ctx2 = lk.lk_create(torus.vertices, torus.offsets)
+    # one request's largest footprint (pack block, then its work buffers too)
+    probe = lk.lk_server_create(None)
+    t = lk.lk_server_submit(probe, ctx, g.pairs)
+    peak, out = 0, np.zeros(g.pairs.shape[0])
+    for _ in range(100000):
+        lk.lk_server_step(probe)
+        peak = max(peak, lk.lk_server_get_stats(probe)["arena_used"])
+        if lk.lk_server_poll(probe, t, None, out, None):
+            break
+    lk.lk_server_destroy(probe)
+    assert peak > 0
+    o = lk.lk_server_default_options()
+    o.arena_bytes = int(peak * 1.5)
+    o.wave_items = 256
+    srv = lk.lk_server_create(o)
+    try:
+        tickets, sizes = [], {}
+        for _ in range(4):
+            t = lk.lk_server_submit(srv, ctx, g.pairs)
+            tickets.append(t)
+            sizes[t] = g.pairs.shape[0]
+        # the four footprints together exceed the arena, so requests had to
+        # wait for room (their pack blocks or their work buffers) ...
+        assert 4 * peak > o.arena_bytes
+        for _ in range(20):
+            lk.lk_server_step(srv)
+            assert lk.lk_server_get_stats(srv)["arena_used"] <= o.arena_bytes   # ... and never overran it
+        res = drain(srv, tickets, sizes)
+        ref = alone(ctx, g.pairs)
+        for t in tickets:
+            assert np.array_equal(res[t][0], ref[0]) and np.array_equal(res[t][1], ref[1])
+        # one pair (a small list) whose work buffers, for its 65k items and
+        # 2.4M chunks, exceed the arena
+        t = lk.lk_server_submit(srv, ctx2, np.ascontiguousarray(torus.pairs))
+        with pytest.raises(lk.LkError) as ei:
+            for _ in range(100000):
+                lk.lk_server_step(srv, wait=True)
+                if lk.lk_server_poll_pairs(srv, t)[0]:
+                    break
+        assert ei.value.status == lk.LK_ERR_OOM
+        assert lk.lk_server_get_stats(srv)["arena_used"] == 0
+    finally:
+        lk.lk_server_destroy(srv)
+        lk.lk_destroy(ctx)
+        lk.lk_destroy(ctx2)
