@@ -1633,10 +1633,9 @@ struct Request {
     size_t scr_off = 0, scr_bytes = 0;   // device: the search's scratch (until packed)
     size_t blk_off = 0, blk_bytes = 0;   // device: the pair list, keys and tasks (until done)
     size_t sum_off = 0, sum_bytes = 0;   // pinned: the totals read back, the tune table
-    long long* h_sum = nullptr;          // [0] candidate pairs, [1..4] lk::PackSums of the packing
+    long long* h_sum = nullptr;          // [0] candidate pairs, [1..6] lk::PackSums: the packing's totals
     int32_t* h_pairs = nullptr;          // pinned copy of the pair list (results)
     int32_t* d_pairs = nullptr;
-    lk::PackSums* d_totals = nullptr;    // [n_tasks] entry of the packing's scan
     ~Request() {
         if (ev) cudaEventDestroy(ev);
     }
@@ -1761,6 +1760,7 @@ size_t pack_layout(int64_t T, PackBufs* b, uintptr_t base) {
 
 // Pinned bytes of a geometry request's totals and tune table.
 constexpr size_t kSumBytes = 64;
+static_assert(sizeof(long long) + sizeof(lk::PackSums) <= kSumBytes, "the totals read back fit their slot");
 size_t geometry_sum_bytes() { return kSumBytes + (size_t)lk::kTuneClasses * lk::kTuneClasses * sizeof(int32_t); }
 
 // A pair-list request packed on the device: its pack block (the pack layout,
@@ -2073,10 +2073,7 @@ bool start_devpack(lk_server* s, Request* r, lk_status* err) {
     }
     const lk::PackParams P{ctx->d_V, ctx->d_R, ctx->d_offsets, r->tuned ? d_tune : nullptr,
                            ctx->opt.accurate_threshold, ctx->opt.tile_rows, (int32_t)ctx->n_loops};
-    const unsigned npk = lk::pls_sort_size(T);
-    lk::launch_pack_keys(pb.pairs, T, P, pb.keys, npk, st);
-    lk::launch_bitonic_sort(pb.keys, npk, st);
-    lk::launch_pack_tasks(pb.keys, pb.pairs, T, P, pb.tasks, pb.sums, pb.scan, pb.scratch, pb.item_begin, st);
+    lk::launch_pack(pb.pairs, T, P, pb.tasks, pb.sums, pb.scan, pb.scratch, pb.item_begin, st);
     check(cudaMemcpyAsync(r->h_sum + 1, pb.scan + T, sizeof(lk::PackSums), cudaMemcpyDeviceToHost, st));
     check(cudaGetLastError());
     check(cudaEventRecord(r->ev, st));
@@ -2145,9 +2142,7 @@ lk_status advance_geometry(lk_server* s) {
             } else {
                 lk::launch_pls_write(sb.keys, L, sb.offsets, pb.pairs, T, st);
             }
-            lk::launch_pack_keys(pb.pairs, T, P, pb.keys, npk, st);
-            lk::launch_bitonic_sort(pb.keys, npk, st);
-            lk::launch_pack_tasks(pb.keys, pb.pairs, T, P, pb.tasks, pb.sums, pb.scan, pb.scratch, pb.item_begin, st);
+            lk::launch_pack(pb.pairs, T, P, pb.tasks, pb.sums, pb.scan, pb.scratch, pb.item_begin, st);
             LK_SRV_CUDA(s, cudaMemcpyAsync(r->h_sum + 1, pb.scan + T, sizeof(lk::PackSums), cudaMemcpyDeviceToHost, st));
             LK_SRV_CUDA(s, cudaGetLastError());
             LK_SRV_CUDA(s, cudaEventRecord(r->ev, st));
@@ -2163,12 +2158,13 @@ lk_status advance_geometry(lk_server* s) {
         lk::PackSums tot;
         std::memcpy(&tot, r->h_sum + 1, sizeof tot);
         const int64_t T = r->n_tasks;
-        if (tot.items > (int64_t)INT32_MAX * 16) {
+        const int64_t n_items = tot.acc_items + tot.fast_items;
+        if (n_items > (int64_t)INT32_MAX * 16) {
             complete_now(s, r, LK_ERR_ARG, "lk_server_submit_geometry: too many work items");
             continue;
         }
         Workspace probe;
-        const size_t need = request_layout(T, tot.items, tot.chunks, false, s->opt.near_capacity, &probe, 0);
+        const size_t need = request_layout(T, n_items, tot.chunks, false, s->opt.near_capacity, &probe, 0);
         if (Arena::round(need) > s->opt.arena_bytes) {
             complete_now(s, r, LK_ERR_OOM, "lk_server_submit_geometry: request larger than the server's arena");
             continue;
@@ -2178,7 +2174,7 @@ lk_status advance_geometry(lk_server* s) {
             continue;
         }
         r->dev_bytes = need;
-        r->n_items = tot.items;
+        r->n_items = n_items;
         r->n_acc_items = tot.acc_items;
         r->n_chunks = tot.chunks;
         request_layout(T, r->n_items, r->n_chunks, false, s->opt.near_capacity, &r->ws,

@@ -284,20 +284,19 @@ struct PackParams {
     int32_t n_loops;               // pairs outside [0, n_loops) or of one loop get status LK_ERR_ARG
 };
 struct PackSums {
-    long long items, chunks, acc_items, segment_pairs;
+    long long acc_n, acc_items;     // accurate-variant pairs and their items
+    long long fast_n, fast_items;   // fast-variant (and invalid) pairs and their items
+    long long chunks, segment_pairs;
 };
 // Entries of the scratch a scan of n values takes (block totals, grand total).
 size_t scan_scratch_count(int64_t n);
 // offsets[0..n] = exclusive scan of counts[0..n-1] (total at [n]).
 void launch_scan_counts(const int32_t* counts, int64_t n, int64_t* offsets, long long* scratch, cudaStream_t s);
-// keys[0..npk) = (sort key << 32 | k) of pair k < n, ~0 above (npk = pls_sort_size(n)).
-void launch_pack_keys(const int32_t* pairs, int64_t n, const PackParams& P, unsigned long long* keys, unsigned npk,
-                      cudaStream_t s);
-// From the sorted keys: tasks[0..n), their counts (sums), the exclusive scan
-// of the counts (scan_out[0..n], totals at [n]) and item_begin[0..n].
-void launch_pack_tasks(const unsigned long long* keys, const int32_t* pairs, int64_t n, const PackParams& P,
-                       PairTask* tasks, PackSums* sums, PackSums* scan_out, PackSums* scratch, int64_t* item_begin,
-                       cudaStream_t s);
+// tasks[0..n) and item_begin[0..n] of the pair list pairs[0..n) (device);
+// scan_out[n] receives the totals.  vals, scan_out ([n + 1]) and scratch
+// (scan_scratch_count(n)) are work space.
+void launch_pack(const int32_t* pairs, int64_t n, const PackParams& P, PairTask* tasks, PackSums* vals,
+                 PackSums* scan_out, PackSums* scratch, int64_t* item_begin, cudaStream_t s);
 void launch_pack_item_task(const int64_t* item_begin, int64_t n_tasks, int64_t n_items, int32_t* item_task,
                            cudaStream_t s);
 int sweep_f64_blocks_per_sm();

@@ -3,17 +3,18 @@
 // Sec. 3.2, Algorithm 2, run on the device), or a served pair list uploaded
 // as it is, laid out as work items without the host packer.
 //
-// The layout is the one the host packer gives the same list (a pair's tiling
-// depends only on its two loop sizes and the tune table; accurate-variant
-// pairs first, then within each variant the largest items first, ties in list
-// order), computed as:
-//   1. per pair its orientation, tile height, items and a 64-bit sort key
-//      (variant, inverse item cost, list index);
-//   2. a bitonic sort of the keys;
-//   3. per sorted position its PairTask and its counts (items, 32-row chunks,
-//      accurate items, segment pairs);
-//   4. an exclusive scan of the counts (item_begin; the totals come last);
-//   5. per work item its task, by binary search in item_begin.
+// Each pair's tiling is the host packer's (it depends only on the pair's two
+// loop sizes and the tune table), so each pair's result is the same; the
+// tasks are ordered accurate-variant pairs first, then fast-variant ones,
+// each in list order (the host packer also puts the largest items first
+// within a variant, which only balances the persistent grid's tail and is
+// left out here to spare the sort):
+//   1. per pair its shape and counts (variant, items, 32-row chunks, segment
+//      pairs);
+//   2. an exclusive scan of the counts: each pair's rank and first item
+//      within its variant, the totals last;
+//   3. per pair its PairTask at its place, and item_begin;
+//   4. per work item its task, by binary search in item_begin.
 // The scans here are plain three-pass block scans (block totals, one block
 // over the totals, block-local scan plus the block's offset), with 64-bit
 // sums, in a fixed order.
@@ -30,11 +31,11 @@ constexpr int kScanPer = 8;
 constexpr int kScanBlock = kScanThreads * kScanPer;   // elements per block
 
 __device__ __forceinline__ PackSums operator+(const PackSums& x, const PackSums& y) {
-    return PackSums{x.items + y.items, x.chunks + y.chunks, x.acc_items + y.acc_items,
-                    x.segment_pairs + y.segment_pairs};
+    return PackSums{x.acc_n + y.acc_n, x.acc_items + y.acc_items, x.fast_n + y.fast_n,
+                    x.fast_items + y.fast_items, x.chunks + y.chunks, x.segment_pairs + y.segment_pairs};
 }
 __device__ __forceinline__ void zero(long long& v) { v = 0; }
-__device__ __forceinline__ void zero(PackSums& v) { v = PackSums{0, 0, 0, 0}; }
+__device__ __forceinline__ void zero(PackSums& v) { v = PackSums{0, 0, 0, 0, 0, 0}; }
 __device__ __forceinline__ long long load(const int32_t* in, int64_t i) { return (long long)in[i]; }
 __device__ __forceinline__ PackSums load(const PackSums* in, int64_t i) { return in[i]; }
 
@@ -196,32 +197,40 @@ __device__ Shape pair_shape(const PackParams& P, int32_t a, int32_t b) {
     return t;
 }
 
-__global__ void pack_keys_kernel(const int32_t* __restrict__ pairs, int64_t n, PackParams P, unsigned npk,
-                                 unsigned long long* __restrict__ keys) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= npk) return;
-    if (k >= n) {
-        keys[k] = ~0ull;
+// Per pair, in list order, its variant and counts: the scan input.  An
+// invalid pair counts as a fast-variant pair with no items.
+__global__ void pack_count_kernel(const int32_t* __restrict__ pairs, int64_t n, PackParams P,
+                                  PackSums* __restrict__ vals) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const Shape t = pair_shape(P, pairs[2 * p], pairs[2 * p + 1]);
+    if (t.status != LK_OK) {
+        vals[p] = PackSums{0, 0, 1, 0, 0, 0};
         return;
     }
-    const Shape t = pair_shape(P, pairs[2 * k], pairs[2 * k + 1]);
-    keys[k] = ((unsigned long long)t.key << 32) | (unsigned long long)k;
+    const long long sp = (long long)t.n_rows * t.n_cols;
+    vals[p] = t.accurate ? PackSums{1, t.items, 0, 0, t.chunks, sp} : PackSums{0, 0, 1, t.items, t.chunks, sp};
 }
 
-__global__ void pack_tasks_kernel(const unsigned long long* __restrict__ keys, const int32_t* __restrict__ pairs,
-                                  int64_t n, PackParams P, PairTask* __restrict__ tasks,
-                                  PackSums* __restrict__ sums) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int32_t p = (int32_t)(keys[k] & 0xffffffffu);
+// Per pair its task, at its rank within its variant (accurate-variant pairs
+// first, list order within each), and its first item.
+__global__ void pack_place_kernel(const int32_t* __restrict__ pairs, int64_t n, PackParams P,
+                                  const PackSums* __restrict__ scan, PairTask* __restrict__ tasks,
+                                  int64_t* __restrict__ item_begin) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const PackSums e = scan[p], tot = scan[n];
+    if (p == 0) item_begin[n] = tot.acc_items + tot.fast_items;
     const Shape t = pair_shape(P, pairs[2 * p], pairs[2 * p + 1]);
+    const bool acc = t.status == LK_OK && t.accurate;
+    const int64_t k = acc ? e.acc_n : tot.acc_n + e.fast_n;
+    item_begin[k] = acc ? e.acc_items : tot.acc_items + e.fast_items;
     PairTask q{};
+    q.out_index = (int32_t)p;
+    q.scale = 1.0f;
     if (t.status != LK_OK) {
-        q.out_index = p;
         q.status = t.status;
-        q.scale = 1.0f;
         tasks[k] = q;
-        sums[k] = PackSums{0, 0, 0, 0};
         return;
     }
     q.V = P.V;
@@ -234,17 +243,9 @@ __global__ void pack_tasks_kernel(const unsigned long long* __restrict__ keys, c
     q.n_cols = t.n_cols;
     q.tile_rows = t.tile_rows;
     q.col_tiles = t.col_tiles;
-    q.out_index = p;
     q.status = 0;
     q.accurate = t.accurate;
-    q.scale = 1.0f;
     tasks[k] = q;
-    sums[k] = PackSums{t.items, t.chunks, t.accurate ? t.items : 0, (long long)t.n_rows * t.n_cols};
-}
-
-__global__ void pack_item_begin_kernel(const PackSums* __restrict__ scan, int64_t n, int64_t* __restrict__ item_begin) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k <= n) item_begin[k] = scan[k].items;
 }
 
 // item_task[i] = the task k with item_begin[k] <= i < item_begin[k + 1].
@@ -269,18 +270,13 @@ void launch_scan_counts(const int32_t* counts, int64_t n, int64_t* offsets, long
     scan<long long, int32_t>(counts, n, reinterpret_cast<long long*>(offsets), scratch, s);
 }
 
-void launch_pack_keys(const int32_t* pairs, int64_t n, const PackParams& P, unsigned long long* keys, unsigned npk,
-                      cudaStream_t s) {
-    pack_keys_kernel<<<(npk + 255) / 256, 256, 0, s>>>(pairs, n, P, npk, keys);
-}
-
-void launch_pack_tasks(const unsigned long long* keys, const int32_t* pairs, int64_t n, const PackParams& P,
-                       PairTask* tasks, PackSums* sums, PackSums* scan_out, PackSums* scratch, int64_t* item_begin,
-                       cudaStream_t s) {
+void launch_pack(const int32_t* pairs, int64_t n, const PackParams& P, PairTask* tasks, PackSums* vals,
+                 PackSums* scan_out, PackSums* scratch, int64_t* item_begin, cudaStream_t s) {
     if (n <= 0) return;
-    pack_tasks_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, pairs, n, P, tasks, sums);
-    scan<PackSums, PackSums>(sums, n, scan_out, scratch, s);
-    pack_item_begin_kernel<<<(unsigned)((n + 256) / 256), 256, 0, s>>>(scan_out, n, item_begin);
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    pack_count_kernel<<<blocks, 256, 0, s>>>(pairs, n, P, vals);
+    scan<PackSums, PackSums>(vals, n, scan_out, scratch, s);
+    pack_place_kernel<<<blocks, 256, 0, s>>>(pairs, n, P, scan_out, tasks, item_begin);
 }
 
 void launch_pack_item_task(const int64_t* item_begin, int64_t n_tasks, int64_t n_items, int32_t* item_task,
