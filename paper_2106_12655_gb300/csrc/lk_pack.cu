@@ -15,9 +15,9 @@
 //      within its variant, the totals last;
 //   3. per pair its PairTask at its place, and item_begin;
 //   4. per work item its task, by binary search in item_begin.
-// The scans here are plain three-pass block scans (block totals, one block
-// over the totals, block-local scan plus the block's offset), with 64-bit
-// sums, in a fixed order.
+// The scans here sum 64-bit integers in a fixed order: one block for up to
+// 2^16 elements, else three passes (block totals, one block over the
+// totals, block-local scan plus the block's offset).
 #include <algorithm>
 
 #include "lk.h"
@@ -127,8 +127,73 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const In* __re
     if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = block_sums[nb];
 }
 
+// One block of 512 threads for lists of up to 2^14 elements (a served
+// request's pairs): rounds of 512 coalesced elements, each scanned by warp
+// shuffles and a scan of the 16 warp totals, with a carry from round to
+// round; the same sums in the same fixed order every time.
+constexpr int kScanSingleThreads = 512;
+constexpr int64_t kScanSingleMax = (int64_t)1 << 14;
+
+__device__ __forceinline__ long long minus(long long a, long long b) { return a - b; }
+__device__ __forceinline__ PackSums minus(const PackSums& a, const PackSums& b) {
+    return PackSums{a.acc_n - b.acc_n, a.acc_items - b.acc_items, a.fast_n - b.fast_n,
+                    a.fast_items - b.fast_items, a.chunks - b.chunks, a.segment_pairs - b.segment_pairs};
+}
+__device__ __forceinline__ long long shfl_up(long long v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ PackSums shfl_up(const PackSums& v, int d) {
+    return PackSums{shfl_up(v.acc_n, d), shfl_up(v.acc_items, d), shfl_up(v.fast_n, d),
+                    shfl_up(v.fast_items, d), shfl_up(v.chunks, d), shfl_up(v.segment_pairs, d)};
+}
+
+template <class T, class In>
+__global__ void __launch_bounds__(kScanSingleThreads) scan_single_kernel(const In* __restrict__ in, int64_t n,
+                                                                         T* __restrict__ out) {
+    __shared__ T warp_sum[kScanSingleThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    T carry;
+    zero(carry);
+    for (int64_t base = 0; base < n; base += kScanSingleThreads) {
+        const int64_t i = base + t;
+        T v;
+        zero(v);
+        if (i < n) v = load(in, i);
+        T x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const T y = shfl_up(x, d);
+            if (lane >= d) x = x + y;
+        }
+        if (lane == 31) warp_sum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            T z;
+            zero(z);
+            if (lane < kScanSingleThreads / 32) z = warp_sum[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const T y = shfl_up(z, d);
+                if (lane >= d) z = z + y;
+            }
+            if (lane < kScanSingleThreads / 32) warp_sum[lane] = z;
+        }
+        __syncthreads();
+        T before;
+        zero(before);
+        if (w > 0) before = warp_sum[w - 1];
+        // exclusive: the inclusive sum less this element (integer sums: exact)
+        if (i < n) out[i] = carry + before + minus(x, v);
+        carry = carry + warp_sum[kScanSingleThreads / 32 - 1];
+        __syncthreads();
+    }
+    if (t == 0) out[n] = carry;
+}
+
 template <class T, class In>
 void scan(const In* in, int64_t n, T* out, T* scratch, cudaStream_t s) {
+    if (n <= kScanSingleMax) {
+        scan_single_kernel<T, In><<<1, kScanSingleThreads, 0, s>>>(in, n, out);
+        return;
+    }
     const int64_t nb = std::max<int64_t>(1, (n + kScanBlock - 1) / kScanBlock);
     scan_reduce_kernel<T, In><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, scratch);
     scan_blocks_kernel<T><<<1, kScanThreads, 0, s>>>(scratch, nb);
