@@ -152,11 +152,14 @@ __global__ void __launch_bounds__(kScanSingleThreads) scan_single_kernel(const I
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     T carry;
     zero(carry);
+    T next;                                   // the next round's element, loaded a round ahead
+    zero(next);
+    if (t < n) next = load(in, t);
     for (int64_t base = 0; base < n; base += kScanSingleThreads) {
         const int64_t i = base + t;
-        T v;
-        zero(v);
-        if (i < n) v = load(in, i);
+        const T v = next;
+        zero(next);
+        if (i + kScanSingleThreads < n) next = load(in, i + kScanSingleThreads);
         T x = v;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
