@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--precise-only", action="store_true",
                     help="verify one woundball pair (nu = 10^3, 2 x 10^5 segments) twice, which the precise "
                          "variant sums: for profiling that kernel")
+    ap.add_argument("--accurate-only", action="store_true",
+                    help="verify one (5,7) torus link of 2 x 100,000 segments (the accurate variant) three "
+                         "times: for profiling that variant of the bulk sweep")
     ap.add_argument("--serving-only", action="store_true",
                     help="the serving capacity alone (closed loop of 32, --serving-requests requests after 40 "
                          "warm-up ones): for launch lists under a profiler")
@@ -1198,6 +1201,32 @@ def run_precise_only(args):
                       "error_estimate": float(est[0]), "precise_pairs": stats["precise_pairs"]}), flush=True)
 
 
+def run_accurate_only(args):
+    """One pair that takes the bulk sweep's accurate variant (10^10 segment
+    pairs) verified three times (CUDA-event time of the last)."""
+    import torch
+    from paper_2106_12655_gb300 import build as B
+    from paper_2106_12655_gb300 import lk
+    from paper_2106_12655_gb300 import workloads as W
+
+    B.build()
+    lk.load()
+    g = W.torus_link(5, 7, 100_000, dtype=np.float32)
+    stream = torch.cuda.current_stream()
+    v = torch.from_numpy(g.vertices).cuda()
+    off = torch.from_numpy(g.offsets).cuda()
+    ctx = lk.lk_create(v, off, None, stream)
+    try:
+        pd = torch.from_numpy(g.pairs).pin_memory()
+        ms, lo, raw, st, est = timed_verify(ctx, pd, 1, stream, 2, 1, v.device)
+        stats = lk.lk_get_stats(ctx)
+    finally:
+        lk.lk_destroy(ctx)
+    print(json.dumps({"workload": "torus link (5,7), 2 x 100,000 segments", "segment_pairs": g.segment_pairs(),
+                      "ms": ms[0], "raw": float(raw[0]), "lk": int(lo[0]), "status": int(st[0]),
+                      "error_estimate": float(est[0]), "precise_pairs": stats["precise_pairs"]}), flush=True)
+
+
 def run_serving_only(args):
     """Closed-loop serving capacity on the six resident piles, alone."""
     from paper_2106_12655_gb300 import build as B
@@ -1228,6 +1257,9 @@ def main():
         return
     if args.serving_only:
         run_serving_only(args)
+        return
+    if args.accurate_only:
+        run_accurate_only(args)
         return
     if args.impl == "reference":
         run_reference(args)
